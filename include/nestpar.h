@@ -1,0 +1,226 @@
+/*
+ * nestpar.h: C ABI of a GB300 (sm_103a) library for irregular nested-parallel
+ * work, following "A Compiler Framework for Optimizing Dynamic Parallelism on
+ * GPUs" (arXiv 2201.02789).
+ *
+ * The problem (Section II-A): each parent thread discovers a data-dependent
+ * amount of nested work, N child items, and in the dynamic-parallelism form
+ * launches a child grid of ceil(N / bDim) blocks with its own arguments. The
+ * library runs that work in every form the paper defines:
+ *
+ *   no dynamic parallelism: the parent loops over its children (the "No CDP"
+ *       baseline of Section VII; no launch site is compiled into that kernel);
+ *   plain CDP: one device-side launch per parent (Section II-A);
+ *   thresholding: launch only when N >= threshold, else run the children
+ *       serially in the parent thread (Section III);
+ *   coarsening: each child block runs `cfactor` consecutive original child
+ *       blocks of the same parent (Section IV);
+ *   aggregation: the child grids of a warp, a block, a group of blocks
+ *       (multi-block granularity, Section V-A) or the whole parent grid
+ *       (Section II-B) are combined into one grid; each aggregated child
+ *       block finds its parent by a search over the scanned block counts
+ *       (disaggregation, Section II-B); an aggregation threshold (Section
+ *       V-B) lets small warp/block groups launch directly instead.
+ *   The three transformations compose in the paper's order T -> C -> A
+ *   (Section VI).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an np_status. Argument errors are detected on
+ *     the host and returned at once (NP_ERR_INVALID); nothing is enqueued then.
+ *   - Arrays passed by pointer are caller-owned device memory unless the name
+ *     ends in _host. They must stay valid until the work on `stream` is done.
+ *     The context owns its workspace (frontiers, aggregation records, look-back
+ *     tile states, the device error word and counters).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream). If `stats` is non-NULL the call
+ *     waits for the stream, fills *stats and returns the device-side status.
+ *     Otherwise device-side errors are reported by the next np_sync().
+ *   - Device-side errors: NP_ERR_LAUNCH (a device launch was refused, for
+ *     example by the pending-launch limit; that parent's children then ran
+ *     serially in the parent, so results stay exact), NP_ERR_TIMEOUT (a bounded
+ *     wait in a look-back scan expired; results are not trustworthy),
+ *     NP_ERR_CAPACITY (tessellation output too small).
+ *   - One context serves one stream at a time: calls that overlap on the GPU
+ *     through the same context race on its workspace.
+ */
+#ifndef NESTPAR_H
+#define NESTPAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t np_status;
+#define NP_OK 0
+#define NP_ERR_INVALID 1      /* bad argument (null pointer, size, config field) */
+#define NP_ERR_CUDA 2         /* a host-side CUDA call failed */
+#define NP_ERR_NOMEM 3        /* device workspace allocation failed */
+#define NP_ERR_CAPACITY 4     /* tessellation output buffer too small */
+#define NP_ERR_LAUNCH 5       /* a device-side launch was refused (work ran serially) */
+#define NP_ERR_TIMEOUT 6      /* a bounded device-side wait expired */
+#define NP_ERR_UNSUPPORTED 7  /* the configuration is not available on this device */
+
+/* ---- configuration (Sections III-V; the paper's _THRESHOLD/_CFACTOR macros
+ *      and aggregation-granularity choice become runtime fields) ---- */
+#define NP_VARIANT_NODP 0     /* parents loop over their children; no launch code */
+#define NP_VARIANT_CDP 1      /* dynamic parallelism with optional T, C and A */
+
+#define NP_GRAN_NONE 0        /* one child grid per launching parent */
+#define NP_GRAN_WARP 1        /* one aggregated grid per warp of parents */
+#define NP_GRAN_BLOCK 2       /* one aggregated grid per parent block */
+#define NP_GRAN_MULTIBLOCK 3  /* one aggregated grid per group of group_blocks parent blocks */
+#define NP_GRAN_GRID_DEVICE 4 /* one aggregated grid per parent grid, launched by its last block */
+#define NP_GRAN_GRID_HOST 5   /* one aggregated grid per parent grid, enqueued after it on the stream */
+
+#define NP_SCAN_LOOKBACK 0    /* multi-block/grid scan by decoupled look-back (records in parent order) */
+#define NP_SCAN_ATOMIC 1      /* the paper's packed 64-bit atomicAdd (records in arrival order) */
+
+#define NP_DRIVER_AUTO 0      /* conditional-while CUDA graph when no device launch is needed, else host-replayed graph chunks */
+#define NP_DRIVER_HOST 1      /* host loop: one level per launch, count read back after each (the paper's form) */
+#define NP_DRIVER_CHUNK 2     /* host-replayed CUDA graph of `unroll` levels, count read back after each chunk */
+#define NP_DRIVER_WHILE 3     /* conditional-while CUDA graph (NODP and GRID_HOST only) */
+
+typedef struct np_config {
+  int32_t variant;       /* NP_VARIANT_* */
+  int32_t threshold;     /* launch iff N >= threshold (values <= 1: every parent with N >= 1);
+                            INT32_MAX: never launch (Section III) */
+  int32_t cfactor;       /* coarsening factor: 1, 2, 4, 8 or 16 (Section IV) */
+  int32_t granularity;   /* NP_GRAN_* (Sections II-B, V-A) */
+  int32_t group_blocks;  /* parent blocks per group at NP_GRAN_MULTIBLOCK (>= 1) */
+  int32_t agg_threshold; /* warp/block granularity: groups with fewer launching parents
+                            launch directly (Section V-B); 0 = off */
+  int32_t child_block;   /* child block size bDim: multiple of 32 in [32, 1024] */
+  int32_t parent_block;  /* parent block size: multiple of 32 in [64, 512] */
+  int32_t scan;          /* NP_SCAN_* */
+  int32_t driver;        /* NP_DRIVER_* (level loop of np_bfs / np_sssp) */
+  int32_t unroll;        /* levels per graph chunk or per while-body, 1..16 */
+  int32_t parent_grid;   /* persistent parent CTAs; 0 = resident capacity */
+  int32_t reserved[4];   /* must be zero */
+} np_config;
+
+/* Fills the library defaults: CDP, threshold 128, cfactor 8, grid-host
+ * aggregation, look-back scan, child block 256, parent block 256, AUTO driver. */
+np_status np_config_default(np_config *cfg);
+
+/* ---- problem descriptions ---- */
+typedef struct np_csr {       /* CSR digraph, device pointers */
+  const int32_t *row_ptr;     /* [n + 1], non-decreasing, row_ptr[0] = 0, row_ptr[n] = m */
+  const int32_t *col_idx;     /* [m], values in [0, n) */
+  const uint32_t *weights;    /* [m] or NULL (required by SSSP) */
+  int32_t n;                  /* vertices, >= 1 */
+  int64_t m;                  /* edges, 0 <= m < 2^31 */
+} np_csr;
+
+typedef struct np_stats {     /* device-side counters of the last call */
+  uint64_t levels;            /* non-empty levels / iterations run */
+  uint64_t parents;           /* parent threads that ran (frontier pops) */
+  uint64_t serial_parents;    /* parents with N > 0 that serialised their children */
+  uint64_t launch_parents;    /* parents whose children ran in a child grid */
+  uint64_t device_launches;   /* device-side kernel launches performed */
+  uint64_t aggregated_grids;  /* of which aggregated child grids */
+  uint64_t child_blocks;      /* coarsened child blocks executed */
+  uint64_t items;             /* child items executed (edges visited/relaxed, points) */
+  uint64_t pushes;            /* vertices appended to frontiers */
+  uint64_t launch_failures;   /* refused device launches (serialised instead) */
+  uint64_t timeouts;          /* expired bounded waits */
+  uint32_t error;             /* device error bits: 1 launch, 2 timeout, 4 capacity */
+  uint32_t reserved;
+} np_stats;
+
+typedef struct np_ctx np_ctx;
+
+/* Creates a context on `device` (made current for the calls that use it).
+ * Raises the device-runtime pending-launch limit to what plain CDP needs. */
+np_status np_create(np_ctx **out, int32_t device);
+np_status np_destroy(np_ctx *ctx);
+
+/* Bytes of device workspace a call with up to `max_parents` parents per level
+ * needs under `cfg` (the context allocates it on first use and keeps it). */
+np_status np_workspace_size(int64_t max_parents, const np_config *cfg, size_t *bytes);
+
+/* Waits for `stream`, returns the sticky device-side status of the context
+ * (and clears it) and, if `stats` is non-NULL, the counters of the last call. */
+np_status np_sync(np_ctx *ctx, void *stream, np_stats *stats);
+
+/* Breadth-first search from `src` (Section VII, BFS benchmark): level[v] =
+ * hop distance from src, -1 if unreachable; level is fully overwritten.
+ * Parent = frontier vertex u, N = out-degree of u, child item = edge u->v,
+ * which claims v (level -1 -> L+1) and appends it to the next frontier. */
+np_status np_bfs(np_ctx *ctx, const np_csr *g, int32_t src, int32_t *level,
+                 const np_config *cfg, void *stream, np_stats *stats);
+
+/* Single-source shortest paths from `src` by frontier Bellman-Ford (Section
+ * VII, SSSP benchmark): dist[v] = least uint32 weight sum, UINT32_MAX if
+ * unreachable. Child item = edge relaxation by atomic minimum; an improved
+ * vertex joins the next frontier once per iteration. Path sums must stay
+ * below 2^32 - 1. */
+np_status np_sssp(np_ctx *ctx, const np_csr *g, int32_t src, uint32_t *dist,
+                  const np_config *cfg, void *stream, np_stats *stats);
+
+/* Quadratic Bezier tessellation (Section VII, BT benchmark). ctrl is
+ * float[ncurves][3][2]. Parent = curve c with curvature
+ * kappa = |P0 - 2P1 + P2| / |P2 - P0| and N = clamp(ceil(sqrt(kappa)*64), 4, 4096)
+ * (computed in FP64 with correctly rounded operations; zero chord: 4096 if the
+ * second difference is non-zero, else 4). offsets[0..ncurves] receives the
+ * curve-order exclusive scan of N (offsets[ncurves] = total). Child item j
+ * writes points[offsets[c] + j] = B(j / (N - 1)) in FP32. If the total
+ * exceeds `cap`, curves that do not fit are skipped and NP_ERR_CAPACITY is
+ * reported; offsets are always complete. */
+np_status np_bezier(np_ctx *ctx, const float *ctrl, int32_t ncurves, int32_t *offsets,
+                    float *points, int64_t cap, const np_config *cfg, void *stream,
+                    np_stats *stats);
+
+/* ---- one nesting pass over an explicit parent set (Section II-A) ---- */
+#define NP_COUNT_CSR_DEGREE 0   /* N = row_ptr[p+1] - row_ptr[p], child i -> edge row_ptr[p] + i */
+#define NP_COUNT_BEZIER 1       /* N = the tessellation point count of curve p */
+#define NP_BODY_BFS_VISIT 0     /* claim col[e] with level next_level, append it to `next` */
+#define NP_BODY_SSSP_RELAX 1    /* atomic-min relax col[e]; append improved targets once per `iteration` */
+#define NP_BODY_BEZIER_EVAL 2   /* write point i of curve p at points[offsets-scan + i] */
+
+typedef struct np_parents {
+  const int32_t *ids;     /* device [count] parent ids, or NULL for ids 0..count-1 */
+  int32_t count;          /* >= 0 */
+} np_parents;
+
+typedef struct np_body {
+  int32_t kind;           /* NP_BODY_* (must match the count kind: CSR for BFS/SSSP) */
+  int32_t next_level;     /* BFS: level written to newly claimed vertices */
+  int32_t iteration;      /* SSSP: stamp value of this pass (>= 1, distinct per pass) */
+  int32_t reserved;
+  int32_t *level;         /* BFS: [n] device */
+  uint32_t *dist;         /* SSSP: [n] device */
+  int32_t *stamp;         /* SSSP: [n] device, last pass that appended each vertex */
+  int32_t *next;          /* BFS/SSSP: [n] device, appended vertices */
+  int32_t *next_count;    /* BFS/SSSP: device int, incremented by the appends */
+  const float *ctrl;      /* Bezier: [count][3][2] device (indexed by parent id) */
+  int32_t *offsets;       /* Bezier: [count + 1] device, written (exclusive scan in parent order) */
+  float *points;          /* Bezier: [cap][2] device */
+  int64_t cap;            /* Bezier: capacity of points in points */
+} np_body;
+
+/* Runs the children of every parent once, in the form `cfg` selects. For CSR
+ * counts `g` describes the graph; for Bezier counts `g` may be NULL. */
+np_status np_run_nested(np_ctx *ctx, const np_parents *parents, int32_t count_kind,
+                        const np_csr *g, const np_body *body, const np_config *cfg,
+                        void *stream, np_stats *stats);
+
+/* ---- end to end from host memory: copies inputs in and results out on
+ *      `stream` (pageable or pinned host buffers), waits, returns the status ---- */
+np_status np_bfs_host(np_ctx *ctx, int32_t n, int64_t m, const int32_t *row_ptr_host,
+                      const int32_t *col_idx_host, int32_t src, int32_t *level_host,
+                      const np_config *cfg, void *stream, np_stats *stats);
+np_status np_sssp_host(np_ctx *ctx, int32_t n, int64_t m, const int32_t *row_ptr_host,
+                       const int32_t *col_idx_host, const uint32_t *weights_host, int32_t src,
+                       uint32_t *dist_host, const np_config *cfg, void *stream, np_stats *stats);
+
+const char *np_status_string(np_status s);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int32_t np_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NESTPAR_H */

@@ -1,0 +1,9 @@
+// Kernels of the bfs child body (see np_device.cuh).
+#include "np_table.cuh"
+
+namespace nestpar {
+const BodyKernels& bfs_kernels() {
+  static const BodyKernels t = make_table<BfsBody>();
+  return t;
+}
+}  // namespace nestpar

@@ -1,0 +1,733 @@
+// Device side of the nested-parallelism engine (sm_103a).
+//
+// One "level" runs the children of a set of parents. Parents are processed by
+// persistent CTAs that take tiles of `parent_block` parents from an atomic
+// ticket (tile order = parent order, and a CTA only ever waits on tiles that
+// running CTAs already own). For every parent the child count N is computed
+// (Section III-D: the number of child threads, not gDim * bDim), then:
+//
+//   NODP        the parent loops over its N children (no launch code at all);
+//   N < T       the parent loops over its children (thresholding, Section III-A);
+//   N >= T      the children go to a child grid of ceil(ceil(N/bDim)/CF)
+//               coarsened blocks (coarsening, Section IV-B), launched
+//               per parent (GRAN_NONE) or aggregated (Sections II-B, V-A).
+//
+// Aggregation scans the coarsened block counts of the launching parents of a
+// scope (warp shuffles, a block scan, a decoupled look-back across the tiles
+// of a group of blocks or of the whole grid, or the paper's packed 64-bit
+// atomic), stores one record {parent, row start, N} per launching parent and
+// the scanned block offset, and one thread launches Sum(cg) blocks. Each
+// aggregated child block finds its parent by a k-ary search (k = block size)
+// over the offsets staged through __syncthreads_count, then runs CF original
+// blocks of that parent (disaggregation outside the coarsening loop, Section VI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nestpar {
+
+constexpr int kMaxParentBlock = 512;
+constexpr unsigned kErrLaunch = 1u, kErrTimeout = 2u, kErrCapacity = 4u;
+constexpr int kSpinLimit = 1 << 21;   // polls before a look-back wait gives up
+constexpr unsigned kFull = 0xffffffffu;
+
+enum Gran : int { G_NONE = 0, G_WARP = 1, G_BLOCK = 2, G_MULTIBLOCK = 3, G_GRID_DEVICE = 4,
+                  G_GRID_HOST = 5, G_NODP = 6 };
+enum Stat : int { S_LEVELS, S_PARENTS, S_SERIAL, S_LAUNCHP, S_DEVLAUNCH, S_AGGGRID, S_CBLOCKS,
+                  S_ITEMS, S_PUSHES, S_LFAIL, S_TIMEOUT, S_N };
+
+// Device-resident state of one solve. Level L reads frontier buffer L&1 with
+// count[L%3] and appends to buffer (L+1)&1 / count[(L+1)%3]; the parent
+// kernel of level L zeroes count[(L+2)%3], which level L+1 appends to.
+struct LevelState {
+  int level;
+  int max_levels;
+  unsigned long long epoch;      // tags look-back flags; never reused, so flags need no reset
+  int ticket;                    // next parent tile of the running parent grid
+  int parent_done;               // CTAs of the parent grid that finished
+  int child_done;                // CTAs of the stream-ordered child grid that finished
+  int count[3];
+  int agg_records;               // grid-host aggregation: launching parents of this level
+  int agg_blocks;                // grid-host aggregation: coarsened child blocks of this level
+  unsigned error;
+  unsigned pad;
+  unsigned long long agg_acc;    // grid-host aggregation with the atomic scan: packed totals
+  unsigned long long s[S_N];     // counters (np_stats)
+  int body_iters;                // conditional-while iterations of this solve (bounded)
+  int pad2;
+};
+
+// What a child item needs; passed by value to every child grid.
+struct BodyArgs {
+  const int* col;
+  const unsigned* w;
+  int* level;
+  unsigned* dist;
+  int* stamp;
+  const float* ctrl;
+  float2* points;
+  int* next;
+  int* next_count;
+  LevelState* st;
+  int L;                         // BFS writes L+1; SSSP stamps L+1
+  int pad;
+};
+
+struct Args {
+  LevelState* st;
+  const int* ids;                // fixed-count mode: parent ids (NULL = 0..count-1)
+  int* fr0;
+  int* fr1;
+  int* next_ovr;                 // fixed-count mode: append target
+  int* next_count_ovr;
+  int count_fixed;               // >= 0: fixed-count mode (one pass, no level bookkeeping)
+  int L_fixed;
+  const int* row_ptr;
+  BodyArgs b;
+  int* offsets;
+  long long cap;
+  int4* rec;
+  int* boff;
+  unsigned long long* lb_flag;   // look-back tile states of the aggregation scan
+  uint4* lb_agg;
+  uint4* lb_incl;
+  unsigned long long* ob_flag;   // look-back tile states of the output-offset scan
+  uint4* ob_agg;
+  uint4* ob_incl;
+  int* grp_ctr;                  // multi-block group arrival counters
+  unsigned long long* grp_acc;   // multi-block packed atomic accumulators
+  uint2* grp_total;              // multi-block look-back totals
+  int threshold;
+  int cfactor;
+  int child_block;
+  int group_blocks;              // 0 = whole grid (grid granularity)
+  int agg_threshold;
+  int scan;                      // 0 look-back, 1 atomic
+  int advance;                   // 1: the parent grid's last CTA advances the level
+};
+
+struct AggSeg {
+  const int4* rec;
+  const int* boff;
+  int* fr0;                      // level mode: frontier buffers, to find this level's append target
+  int* fr1;
+  int nrec;
+  int total;
+  int mode;                      // 0: fixed segment; 1: grid-host, look-back totals; 2: grid-host, atomic totals
+  int advance;                   // 1: the child grid's last CTA advances the level
+  int level_mode;                // 1: take L, next and next_count from the level state
+  int pad;
+};
+
+// ---------------------------------------------------------------- primitives
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+__host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+struct V3 {
+  unsigned a, b, c;
+};
+__device__ __forceinline__ V3 v3add(V3 x, V3 y) { return V3{x.a + y.a, x.b + y.b, x.c + y.c}; }
+__device__ __forceinline__ V3 warp_sum3(V3 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.a += __shfl_xor_sync(kFull, v.a, o);
+    v.b += __shfl_xor_sync(kFull, v.b, o);
+    v.c += __shfl_xor_sync(kFull, v.c, o);
+  }
+  return v;
+}
+
+// Decoupled look-back (single-pass prefix scan over tiles): run by one full
+// warp; returns the exclusive prefix of tile `tile` within [first, tile].
+// Flags hold (epoch << 2) | status, status 1 = aggregate published,
+// 2 = inclusive prefix published. Waits are bounded: on expiry the error word
+// gets kErrTimeout and the wait is abandoned (result then wrong, never a hang).
+__device__ inline V3 lookback(unsigned long long* flag, uint4* agg, uint4* incl, int tile, int first,
+                       unsigned long long epoch, V3 mine, LevelState* st) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long fA = (epoch << 2) | 1ull, fP = (epoch << 2) | 2ull;
+  if (tile == first) {
+    if (lane == 0) {
+      incl[tile] = make_uint4(mine.a, mine.b, mine.c, 0u);
+      st_release_u64(&flag[tile], fP);
+    }
+    return V3{0, 0, 0};
+  }
+  if (lane == 0) {
+    agg[tile] = make_uint4(mine.a, mine.b, mine.c, 0u);
+    st_release_u64(&flag[tile], fA);
+  }
+  V3 excl{0, 0, 0};
+  int j = tile - 1;
+  for (;;) {
+    const int idx = j - lane;
+    const bool in = idx >= first;
+    unsigned long long f = fP;
+    bool timed_out = false;
+    if (in) {
+      f = ld_acquire_u64(&flag[idx]);
+      int spins = 0;
+      while ((f >> 2) != epoch || (f & 3ull) == 0ull) {
+        if (++spins > kSpinLimit) {
+          timed_out = true;
+          break;
+        }
+        __nanosleep(32);
+        f = ld_acquire_u64(&flag[idx]);
+      }
+      if (timed_out) {
+        atomicOr(&st->error, kErrTimeout);
+        atomicAdd(&st->s[S_TIMEOUT], 1ull);
+        f = fP;
+      }
+    }
+    const bool isP = (f & 3ull) == 2ull;
+    V3 v{0, 0, 0};
+    if (in && !timed_out) {
+      uint4 x = __ldcg(isP ? &incl[idx] : &agg[idx]);
+      v = V3{x.x, x.y, x.z};
+    }
+    const unsigned pm = __ballot_sync(kFull, isP);
+    const int stop = pm ? __ffs(pm) - 1 : 31;
+    if (lane > stop) v = V3{0, 0, 0};
+    excl = v3add(excl, warp_sum3(v));
+    if (pm) break;
+    j -= 32;
+  }
+  if (lane == 0) {
+    V3 inc = v3add(excl, mine);
+    incl[tile] = make_uint4(inc.a, inc.b, inc.c, 0u);
+    st_release_u64(&flag[tile], fP);
+  }
+  return excl;
+}
+
+// Exclusive scan of two counters over the CTA. Returns this thread's exclusive
+// values and the CTA totals (in all threads). Uses s[0..32].
+__device__ __forceinline__ void block_scan2(unsigned a, unsigned b, unsigned& ea, unsigned& eb,
+                                            unsigned& ta, unsigned& tb, uint2* s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned xa = __shfl_up_sync(kFull, ia, o), xb = __shfl_up_sync(kFull, ib, o);
+    if (lane >= o) {
+      ia += xa;
+      ib += xb;
+    }
+  }
+  if (lane == 31) s[warp] = make_uint2(ia, ib);
+  __syncthreads();
+  if (warp == 0) {
+    uint2 t = lane < nw ? s[lane] : make_uint2(0u, 0u);
+    unsigned xa = t.x, xb = t.y;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned ya = __shfl_up_sync(kFull, xa, o), yb = __shfl_up_sync(kFull, xb, o);
+      if (lane >= o) {
+        xa += ya;
+        xb += yb;
+      }
+    }
+    if (lane < nw) s[lane] = make_uint2(xa - t.x, xb - t.y);   // exclusive warp prefix
+    if (lane == 31) s[32] = make_uint2(xa, xb);               // CTA total
+  }
+  __syncthreads();
+  uint2 wp = s[warp];
+  ea = wp.x + ia - a;
+  eb = wp.y + ib - b;
+  ta = s[32].x;
+  tb = s[32].y;
+  __syncthreads();
+}
+
+// Largest j in [lo, hi) with boff[j] <= B, for strictly increasing boff and
+// boff[lo] <= B. k-ary search with k = blockDim.x: every round each thread
+// tests one sample and __syncthreads_count ranks B among them.
+__device__ __forceinline__ int disaggregate(const int* boff, int lo, int hi, int B) {
+  const int T = blockDim.x, tid = threadIdx.x;
+  while (hi - lo > T) {
+    const int stride = ceil_div(hi - lo, T);
+    const int idx = lo + tid * stride;
+    const bool p = idx < hi && __ldcg(&boff[idx]) <= B;
+    const int c = max(__syncthreads_count(p), 1);   // >= 1 by the precondition; clamped to stay in range
+    lo += (c - 1) * stride;
+    hi = min(hi, lo + stride);
+  }
+  const int idx = lo + tid;
+  const bool p = idx < hi && __ldcg(&boff[idx]) <= B;
+  const int c = max(__syncthreads_count(p), 1);
+  return lo + c - 1;
+}
+
+// Append v to the next frontier when pred holds; one atomic per warp.
+// kFullWarp: all 32 lanes are known to be here (child blocks); otherwise the
+// currently active lanes cooperate (serial loops in diverged parent threads).
+template <bool kFullWarp>
+__device__ __forceinline__ void push_frontier(bool pred, int v, int* next, int* next_count) {
+  const unsigned act = kFullWarp ? kFull : __activemask();
+  const unsigned m = __ballot_sync(act, pred);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(next_count, __popc(m));
+  base = __shfl_sync(act, base, leader);
+  if (pred) next[base + __popc(m & lanemask_lt())] = v;
+}
+
+// ------------------------------------------------------------------- bodies
+
+// BFS (Section VII): child item = out-edge u->v; claims v for level L+1.
+struct BfsBody {
+  static constexpr bool kOffsets = false;
+  struct P {
+    int base;
+  };
+  struct F {
+    int v;
+  };
+  __device__ static void count(const Args& a, int pid, int& base, int& N) {
+    base = __ldg(&a.row_ptr[pid]);
+    N = __ldg(&a.row_ptr[pid + 1]) - base;
+  }
+  __device__ static P parent(const BodyArgs&, int, int base, int) { return P{base}; }
+  __device__ static F fetch(const BodyArgs& b, const P& p, int i) { return F{__ldg(&b.col[p.base + i])}; }
+  template <bool kFullWarp>
+  __device__ static void apply(const BodyArgs& b, const P&, int, const F& f, bool valid) {
+    bool claimed = false;
+    if (valid && b.level[f.v] == -1) claimed = atomicCAS(&b.level[f.v], -1, b.L + 1) == -1;
+    push_frontier<kFullWarp>(claimed, f.v, b.next, b.next_count);
+  }
+};
+
+// SSSP (Section VII): child item = relaxation of out-edge u->v with weight w.
+struct SsspBody {
+  static constexpr bool kOffsets = false;
+  struct P {
+    int base;
+    unsigned du;
+  };
+  struct F {
+    int v;
+    unsigned w;
+  };
+  __device__ static void count(const Args& a, int pid, int& base, int& N) {
+    base = __ldg(&a.row_ptr[pid]);
+    N = __ldg(&a.row_ptr[pid + 1]) - base;
+  }
+  __device__ static P parent(const BodyArgs& b, int pid, int base, int) {
+    return P{base, __ldcg(&b.dist[pid])};
+  }
+  __device__ static F fetch(const BodyArgs& b, const P& p, int i) {
+    return F{__ldg(&b.col[p.base + i]), __ldg(&b.w[p.base + i])};
+  }
+  template <bool kFullWarp>
+  __device__ static void apply(const BodyArgs& b, const P& p, int, const F& f, bool valid) {
+    bool push = false;
+    if (valid && p.du != 0xffffffffu) {
+      unsigned long long s = (unsigned long long)p.du + f.w;
+      unsigned nd = s >= 0xffffffffull ? 0xfffffffeu : (unsigned)s;
+      if (nd < b.dist[f.v]) {
+        unsigned old = atomicMin(&b.dist[f.v], nd);
+        if (nd < old) push = atomicExch(&b.stamp[f.v], b.L + 1) != b.L + 1;
+      }
+    }
+    push_frontier<kFullWarp>(push, f.v, b.next, b.next_count);
+  }
+};
+
+// BT (Section VII): parent = quadratic curve; child item j = point j.
+struct BezierBody {
+  static constexpr bool kOffsets = true;
+  struct P {
+    float x0, y0, x1, y1, x2, y2;
+    int base;
+    float denom;
+  };
+  struct F {};
+  // Point count in FP64 with correctly rounded operations only, so that it is
+  // bit-identical to a serial FP64 evaluation (no contraction into FMA).
+  __device__ static int point_count(const float* p) {
+    const double x0 = p[0], y0 = p[1], x1 = p[2], y1 = p[3], x2 = p[4], y2 = p[5];
+    const double sx = __dadd_rn(__dsub_rn(x0, __dmul_rn(2.0, x1)), x2);
+    const double sy = __dadd_rn(__dsub_rn(y0, __dmul_rn(2.0, y1)), y2);
+    const double cx = __dsub_rn(x2, x0), cy = __dsub_rn(y2, y0);
+    const double s2 = __dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy));
+    const double c2 = __dadd_rn(__dmul_rn(cx, cx), __dmul_rn(cy, cy));
+    if (c2 == 0.0) return s2 > 0.0 ? 4096 : 4;
+    const double kappa = __ddiv_rn(__dsqrt_rn(s2), __dsqrt_rn(c2));
+    const double t = ceil(__dmul_rn(__dsqrt_rn(kappa), 64.0));
+    if (t < 4.0) return 4;
+    if (t > 4096.0) return 4096;
+    return (int)t;
+  }
+  __device__ static void count(const Args& a, int pid, int& base, int& N) {
+    base = 0;
+    N = point_count(a.b.ctrl + 6 * (size_t)pid);
+  }
+  __device__ static P parent(const BodyArgs& b, int pid, int base, int N) {
+    const float* c = b.ctrl + 6 * (size_t)pid;
+    return P{__ldg(c), __ldg(c + 1), __ldg(c + 2), __ldg(c + 3), __ldg(c + 4), __ldg(c + 5), base,
+             (float)(N - 1)};
+  }
+  __device__ static F fetch(const BodyArgs&, const P&, int) { return F{}; }
+  template <bool kFullWarp>
+  __device__ static void apply(const BodyArgs& b, const P& p, int i, const F&, bool valid) {
+    if (!valid) return;
+    const float t = (float)i / p.denom;
+    const float u = 1.0f - t;
+    const float b0 = u * u, b1 = 2.0f * u * t, b2 = t * t;
+    b.points[p.base + i] = make_float2(b0 * p.x0 + b1 * p.x1 + b2 * p.x2, b0 * p.y0 + b1 * p.y1 + b2 * p.y2);
+  }
+};
+
+// --------------------------------------------------------------- child side
+
+// One coarsened child block: CF consecutive original blocks of one parent
+// (Section IV-B; contiguous original blocks). Loads of all CF items are issued
+// before any of them is applied.
+template <class Body, int CF>
+__device__ __forceinline__ void run_coarsened(const BodyArgs& b, const typename Body::P& p, int N, int cb) {
+  const int B = blockDim.x, tid = threadIdx.x;
+  typename Body::F f[CF];
+  bool v[CF];
+#pragma unroll
+  for (int k = 0; k < CF; k++) {
+    const int i = (cb * CF + k) * B + tid;
+    v[k] = i < N;
+    if (v[k]) f[k] = Body::fetch(b, p, i);
+  }
+#pragma unroll
+  for (int k = 0; k < CF; k++) {
+    const int i0 = (cb * CF + k) * B;
+    if (i0 < N) Body::template apply<true>(b, p, i0 + tid, f[k], v[k]);
+  }
+}
+
+// Serial version of a parent's children (thresholding's fallback, the NODP form).
+template <class Body>
+__device__ __forceinline__ void run_serial(const BodyArgs& b, int pid, int base, int N) {
+  const typename Body::P p = Body::parent(b, pid, base, N);
+  for (int i = 0; i < N; i++) Body::template apply<false>(b, p, i, Body::fetch(b, p, i), true);
+}
+
+__device__ __forceinline__ void add_stat(LevelState* st, int k, unsigned long long v) {
+  if (v) atomicAdd(&st->s[k], v);
+}
+
+// Level bookkeeping once a level's grids are done: counters reset, and the
+// level/epoch advance when the level had parents.
+__device__ __forceinline__ void advance_level(LevelState* st) {
+  const int L = st->level;
+  const int c = st->count[L % 3];
+  st->ticket = 0;
+  st->parent_done = 0;
+  st->child_done = 0;
+  st->agg_records = 0;
+  st->agg_blocks = 0;
+  st->agg_acc = 0ull;
+  if (c > 0) {
+    st->s[S_LEVELS] += 1;
+    st->s[S_PUSHES] += (unsigned long long)st->count[(L + 1) % 3];
+    st->level = L + 1;
+    st->epoch += 1;
+  }
+  __threadfence();
+}
+
+// Child grid of one parent (plain CDP, thresholded or coarsened launch).
+template <class Body, int CF>
+__global__ void __launch_bounds__(1024) child_direct(BodyArgs b, int pid, int base, int N) {
+  const typename Body::P p = Body::parent(b, pid, base, N);
+  run_coarsened<Body, CF>(b, p, N, blockIdx.x);
+}
+
+// Aggregated child grid: disaggregation + coarsened body. Persistent over the
+// aggregated blocks when launched with fewer CTAs than blocks (grid-host form,
+// whose size is read from device memory).
+template <class Body, int CF>
+__global__ void __launch_bounds__(1024) child_agg(BodyArgs b, AggSeg s) {
+  int nrec = s.nrec, total = s.total;
+  LevelState* st = b.st;
+  if (s.mode == 1) {
+    nrec = __ldcg(&st->agg_records);
+    total = __ldcg(&st->agg_blocks);
+  } else if (s.mode == 2) {
+    const unsigned long long acc = __ldcg(&st->agg_acc);
+    nrec = (int)(acc >> 40);
+    total = (int)(acc & ((1ull << 40) - 1));
+  }
+  if (s.level_mode) {
+    const int L = __ldcg(&st->level);
+    b.L = L;
+    b.next = (L & 1) ? s.fr0 : s.fr1;
+    b.next_count = &st->count[(L + 1) % 3];
+  }
+  int lo = 0;
+  unsigned long long blocks = 0;
+  for (int B0 = blockIdx.x; B0 < total; B0 += gridDim.x) {
+    const int j = disaggregate(s.boff, lo, nrec, B0);
+    const int4 r = __ldcg(&s.rec[j]);
+    const int off = __ldcg(&s.boff[j]);
+    const typename Body::P p = Body::parent(b, r.x, r.y, r.z);
+    run_coarsened<Body, CF>(b, p, r.z, B0 - off);
+    lo = j;
+    blocks++;
+  }
+  if (s.mode != 0) {
+    // persistent (grid-host) form: count its blocks here; device-launched
+    // grids are counted by the launching parent
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      add_stat(st, S_CBLOCKS, blocks);
+      if (s.advance) {
+        __threadfence();
+        if (atomicAdd(&st->child_done, 1) == (int)gridDim.x - 1) {
+          __threadfence();
+          advance_level(st);
+        }
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------- parent side
+
+template <class Body, int CF>
+__device__ __forceinline__ void launch_direct(const BodyArgs& b, int pid, int base, int N, int child_block,
+                                              unsigned* s_stat) {
+  const int cg = ceil_div(ceil_div(N, child_block), CF);
+  child_direct<Body, CF><<<cg, child_block, 0, cudaStreamFireAndForget>>>(b, pid, base, N);
+  if (cudaGetLastError() != cudaSuccess) {
+    atomicOr(&b.st->error, kErrLaunch);
+    atomicAdd(&s_stat[S_LFAIL], 1u);
+    run_serial<Body>(b, pid, base, N);
+  } else {
+    atomicAdd(&s_stat[S_DEVLAUNCH], 1u);
+    atomicAdd(&s_stat[S_CBLOCKS], (unsigned)cg);
+  }
+}
+
+template <class Body, int CF>
+__device__ __forceinline__ void launch_aggregated(const BodyArgs& b, const int4* rec, const int* boff, int nrec,
+                                                  int total, int child_block, unsigned* s_stat) {
+  AggSeg s{rec, boff, nullptr, nullptr, nrec, total, 0, 0, 0, 0};
+  child_agg<Body, CF><<<total, child_block, 0, cudaStreamFireAndForget>>>(b, s);
+  if (cudaGetLastError() != cudaSuccess) {
+    // run the aggregated grid's work in this thread: parent by parent, serially
+    atomicOr(&b.st->error, kErrLaunch);
+    atomicAdd(&s_stat[S_LFAIL], 1u);
+    for (int j = 0; j < nrec; j++) {
+      const int4 r = __ldcg(&rec[j]);
+      run_serial<Body>(b, r.x, r.y, r.z);
+    }
+  } else {
+    atomicAdd(&s_stat[S_DEVLAUNCH], 1u);
+    atomicAdd(&s_stat[S_AGGGRID], 1u);
+    atomicAdd(&s_stat[S_CBLOCKS], (unsigned)total);
+  }
+}
+
+// The parent kernel of one level. GRAN selects the form; CF is the coarsening
+// factor of the child kernel it launches (device-launch forms only).
+template <class Body, int GRAN, int CF>
+__global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
+  __shared__ int s_tile;
+  __shared__ uint2 s_scan[33];
+  __shared__ V3 s_v3;
+  __shared__ unsigned s_stat[S_N];
+  const int tid = threadIdx.x, PB = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  LevelState* st = a.st;
+  const bool fixed = a.count_fixed >= 0;
+  const int L = fixed ? a.L_fixed : __ldcg(&st->level);
+  const unsigned long long epoch = __ldcg(&st->epoch);
+  const int count = fixed ? a.count_fixed : __ldcg(&st->count[L % 3]);
+  if (!fixed && blockIdx.x == 0 && tid == 0) st->count[(L + 2) % 3] = 0;
+  if (count <= 0) return;
+  const int* ids = fixed ? a.ids : ((L & 1) ? a.fr1 : a.fr0);
+  BodyArgs b = a.b;
+  b.L = L;
+  b.next = fixed ? a.next_ovr : ((L & 1) ? a.fr0 : a.fr1);
+  b.next_count = fixed ? a.next_count_ovr : &st->count[(L + 1) % 3];
+  const int ntiles = ceil_div(count, PB);
+  const int T = a.threshold < 1 ? 1 : a.threshold;
+  const int CB = a.child_block;
+  if (tid < S_N) s_stat[tid] = 0;
+  __syncthreads();
+
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(&st->ticket, 1);
+    __syncthreads();
+    const int tile = s_tile;
+    __syncthreads();
+    if (tile >= ntiles) break;
+    const int i = tile * PB + tid;
+    const bool valid = i < count;
+    int pid = 0, base = 0, N = 0;
+    if (valid) {
+      pid = ids ? __ldcg(&ids[i]) : i;
+      Body::count(a, pid, base, N);
+    }
+    if constexpr (Body::kOffsets) {
+      // output offsets: exclusive scan of N over all parents, in parent order
+      unsigned e0, e1, t0, t1;
+      block_scan2((unsigned)N, 0u, e0, e1, t0, t1, s_scan);
+      if (warp == 0) {
+        V3 x = lookback(a.ob_flag, a.ob_agg, a.ob_incl, tile, 0, epoch, V3{t0, 0u, 0u}, st);
+        if (lane == 0) s_v3 = x;
+      }
+      __syncthreads();
+      const unsigned tile_base = s_v3.a;
+      __syncthreads();
+      base = (int)(tile_base + e0);
+      if (valid) a.offsets[i] = base;
+      if (tile == ntiles - 1 && tid == 0) a.offsets[count] = (int)(tile_base + t0);
+      if (valid && (long long)base + N > a.cap) {
+        atomicOr(&st->error, kErrCapacity);
+        N = 0;
+      }
+    }
+    if (valid) {
+      atomicAdd(&s_stat[S_PARENTS], 1u);
+      atomicAdd(&s_stat[S_ITEMS], (unsigned)N);
+    }
+    if constexpr (GRAN == G_NODP) {
+      if (valid && N > 0) {
+        atomicAdd(&s_stat[S_SERIAL], 1u);
+        run_serial<Body>(b, pid, base, N);
+      }
+    } else {
+      const bool launch = valid && N >= T;
+      if (valid && !launch && N > 0) {
+        atomicAdd(&s_stat[S_SERIAL], 1u);
+        run_serial<Body>(b, pid, base, N);
+      }
+      if (launch) atomicAdd(&s_stat[S_LAUNCHP], 1u);
+      const unsigned cg = launch ? (unsigned)ceil_div(ceil_div(N, CB), a.cfactor) : 0u;
+      if constexpr (GRAN == G_NONE) {
+        if (launch) launch_direct<Body, CF>(b, pid, base, N, CB, s_stat);
+      } else if constexpr (GRAN == G_WARP) {
+        const unsigned m = __ballot_sync(kFull, launch);
+        const int np = __popc(m);
+        if (np > 0 && np < a.agg_threshold) {
+          if (launch) launch_direct<Body, CF>(b, pid, base, N, CB, s_stat);
+        } else if (np > 0) {
+          unsigned inc = cg;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            unsigned x = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += x;
+          }
+          const unsigned total = __shfl_sync(kFull, inc, 31);
+          const int seg = tile * PB + warp * 32;
+          const int slot = __popc(m & lanemask_lt());
+          if (launch) {
+            a.rec[seg + slot] = make_int4(pid, base, N, 0);
+            a.boff[seg + slot] = (int)(inc - cg);
+          }
+          __threadfence();
+          __syncwarp();
+          if (lane == 31 - __clz(m))
+            launch_aggregated<Body, CF>(b, a.rec + seg, a.boff + seg, np, (int)total, CB, s_stat);
+        }
+      } else if constexpr (GRAN == G_BLOCK) {
+        unsigned ea, eb, ta, tb;
+        block_scan2(launch ? 1u : 0u, cg, ea, eb, ta, tb, s_scan);
+        if ((int)ta < a.agg_threshold) {
+          if (launch) launch_direct<Body, CF>(b, pid, base, N, CB, s_stat);
+        } else {
+          const int seg = tile * PB;
+          if (launch) {
+            a.rec[seg + ea] = make_int4(pid, base, N, 0);
+            a.boff[seg + ea] = (int)eb;
+          }
+          __threadfence();
+          __syncthreads();
+          if (tid == 0 && ta > 0) launch_aggregated<Body, CF>(b, a.rec + seg, a.boff + seg, (int)ta, (int)tb, CB, s_stat);
+        }
+      } else {
+        // multi-block / grid granularity: the scope is a group of G tiles
+        const int G = (GRAN == G_GRID_HOST || a.group_blocks <= 0) ? ntiles : a.group_blocks;
+        const int g = tile / G, first = g * G, gsize = min(G, ntiles - first);
+        unsigned ea, eb, ta, tb;
+        block_scan2(launch ? 1u : 0u, cg, ea, eb, ta, tb, s_scan);
+        if (a.scan == 0) {
+          if (warp == 0) {
+            V3 x = lookback(a.lb_flag, a.lb_agg, a.lb_incl, tile, first, epoch, V3{ta, tb, 0u}, st);
+            if (lane == 0) s_v3 = x;
+          }
+        } else if (tid == 0) {
+          unsigned long long* acc = (GRAN == G_GRID_HOST) ? &st->agg_acc : &a.grp_acc[g];
+          const unsigned long long old = atomicAdd(acc, ((unsigned long long)ta << 40) | tb);
+          s_v3 = V3{(unsigned)(old >> 40), (unsigned)(old & ((1ull << 40) - 1)), 0u};
+        }
+        __syncthreads();
+        const V3 x = s_v3;
+        const int seg = (GRAN == G_GRID_HOST) ? 0 : first * PB;
+        if (launch) {
+          a.rec[seg + x.a + ea] = make_int4(pid, base, N, 0);
+          a.boff[seg + x.a + ea] = (int)(x.b + eb);
+        }
+        if constexpr (GRAN == G_GRID_HOST) {
+          if (a.scan == 0 && tile == ntiles - 1 && tid == 0) {
+            st->agg_records = (int)(x.a + ta);
+            st->agg_blocks = (int)(x.b + tb);
+          }
+          __syncthreads();
+        } else {
+          if (a.scan == 0 && tile == first + gsize - 1 && tid == 0) a.grp_total[g] = make_uint2(x.a + ta, x.b + tb);
+          __threadfence();
+          __syncthreads();
+          if (tid == 0) {
+            const int old = atomicAdd(&a.grp_ctr[g], 1);
+            if (old == gsize - 1) {
+              __threadfence();
+              unsigned nrec, nblk;
+              if (a.scan == 0) {
+                const uint2 t = __ldcg(&a.grp_total[g]);
+                nrec = t.x;
+                nblk = t.y;
+              } else {
+                const unsigned long long t = atomicExch(&a.grp_acc[g], 0ull);
+                nrec = (unsigned)(t >> 40);
+                nblk = (unsigned)(t & ((1ull << 40) - 1));
+              }
+              a.grp_ctr[g] = 0;
+              if (nrec > 0) launch_aggregated<Body, CF>(b, a.rec + seg, a.boff + seg, (int)nrec, (int)nblk, CB, s_stat);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  __syncthreads();
+  if (tid < S_N && tid != S_LEVELS && tid != S_PUSHES) add_stat(st, tid, s_stat[tid]);
+  if (a.advance) {
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      if (atomicAdd(&st->parent_done, 1) == (int)gridDim.x - 1) {
+        __threadfence();
+        advance_level(st);
+      }
+    }
+  }
+}
+
+}  // namespace nestpar

@@ -1,0 +1,30 @@
+// Host-visible table of the kernels instantiated for one child body.
+#pragma once
+
+namespace nestpar {
+
+constexpr int kNumCF = 5;                     // coarsening factors 1, 2, 4, 8, 16
+inline int cf_index(int cf) {
+  switch (cf) {
+    case 1: return 0;
+    case 2: return 1;
+    case 4: return 2;
+    case 8: return 3;
+    case 16: return 4;
+    default: return -1;
+  }
+}
+
+struct BodyKernels {
+  const void* parent_nodp;                    // parent_kernel<Body, G_NODP, 1>
+  const void* parent_grid_host;               // parent_kernel<Body, G_GRID_HOST, 1>
+  const void* parent[4][kNumCF];              // [NONE, WARP, BLOCK, MULTIBLOCK/GRID_DEVICE][cf]
+  const void* child_direct[kNumCF];
+  const void* child_agg[kNumCF];
+};
+
+const BodyKernels& bfs_kernels();
+const BodyKernels& sssp_kernels();
+const BodyKernels& bezier_kernels();
+
+}  // namespace nestpar

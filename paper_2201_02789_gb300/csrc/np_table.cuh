@@ -1,0 +1,39 @@
+// Instantiates every kernel of one body and fills its table.
+#pragma once
+#include "np_device.cuh"
+#include "np_kernels.h"
+
+namespace nestpar {
+
+template <class Body, int G>
+inline void fill_parent_row(const void* (&row)[kNumCF]) {
+  row[0] = (const void*)parent_kernel<Body, G, 1>;
+  row[1] = (const void*)parent_kernel<Body, G, 2>;
+  row[2] = (const void*)parent_kernel<Body, G, 4>;
+  row[3] = (const void*)parent_kernel<Body, G, 8>;
+  row[4] = (const void*)parent_kernel<Body, G, 16>;
+}
+
+template <class Body>
+inline BodyKernels make_table() {
+  BodyKernels t{};
+  t.parent_nodp = (const void*)parent_kernel<Body, G_NODP, 1>;
+  t.parent_grid_host = (const void*)parent_kernel<Body, G_GRID_HOST, 1>;
+  fill_parent_row<Body, G_NONE>(t.parent[0]);
+  fill_parent_row<Body, G_WARP>(t.parent[1]);
+  fill_parent_row<Body, G_BLOCK>(t.parent[2]);
+  fill_parent_row<Body, G_MULTIBLOCK>(t.parent[3]);
+  t.child_direct[0] = (const void*)child_direct<Body, 1>;
+  t.child_direct[1] = (const void*)child_direct<Body, 2>;
+  t.child_direct[2] = (const void*)child_direct<Body, 4>;
+  t.child_direct[3] = (const void*)child_direct<Body, 8>;
+  t.child_direct[4] = (const void*)child_direct<Body, 16>;
+  t.child_agg[0] = (const void*)child_agg<Body, 1>;
+  t.child_agg[1] = (const void*)child_agg<Body, 2>;
+  t.child_agg[2] = (const void*)child_agg<Body, 4>;
+  t.child_agg[3] = (const void*)child_agg<Body, 8>;
+  t.child_agg[4] = (const void*)child_agg<Body, 16>;
+  return t;
+}
+
+}  // namespace nestpar

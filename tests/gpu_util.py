@@ -1,0 +1,63 @@
+"""Helpers for the GPU tests: device copies of generated inputs and a shared context."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from paper_2201_02789_gb300 import nestpar as npb
+
+
+class DevGraph:
+    """A generated CSR graph copied to the GPU, with its np_csr descriptor."""
+
+    def __init__(self, g, device="cuda:0"):
+        self.g = g
+        self.n, self.m = g.n, g.m
+        self.row_ptr = torch.from_numpy(np.ascontiguousarray(g.row_ptr)).to(device)
+        self.col = torch.from_numpy(np.ascontiguousarray(g.col) if g.m else np.zeros(1, np.int32)).to(device)
+        w = g.w if g.w is not None else np.ones(g.m, np.uint32)
+        self.w = torch.from_numpy(np.ascontiguousarray(w).view(np.int32) if g.m else np.zeros(1, np.int32)).to(device)
+        self.csr = npb.make_csr(self.row_ptr, self.col, self.w, n=g.n, m=g.m)
+
+
+def bfs(ctx, dg: DevGraph, src: int, cfg, stats=False):
+    level = torch.empty(dg.n, dtype=torch.int32, device=dg.row_ptr.device)
+    r = npb.np_bfs(ctx.handle, dg.csr, src, level, cfg, stats=stats)
+    out = level.cpu().numpy()
+    return (out, r[1]) if stats else out
+
+
+def sssp(ctx, dg: DevGraph, src: int, cfg, stats=False):
+    dist = torch.empty(dg.n, dtype=torch.int32, device=dg.row_ptr.device)
+    r = npb.np_sssp(ctx.handle, dg.csr, src, dist, cfg, stats=stats)
+    out = dist.cpu().numpy().view(np.uint32)
+    return (out, r[1]) if stats else out
+
+
+def bezier(ctx, ctrl: np.ndarray, cfg, cap=None, stats=False, check=True):
+    dev = torch.device("cuda:0")
+    nc = ctrl.shape[0]
+    c_d = torch.from_numpy(np.ascontiguousarray(ctrl)).to(dev)
+    off = torch.full((nc + 1,), -7, dtype=torch.int32, device=dev)
+    if cap is None:
+        cap = nc * 4096
+    pts = torch.full((max(cap, 1), 2), float("nan"), dtype=torch.float32, device=dev)
+    r = npb.np_bezier(ctx.handle, c_d, nc, off, pts, cap, cfg, stats=True, check=check)
+    status, st = r
+    return status, off.cpu().numpy(), pts.cpu().numpy(), st
+
+
+def form_grid():
+    """(name, config) pairs spanning variant x threshold x cfactor x granularity."""
+    out = [("nodp", npb.config("nodp"))]
+    grans = [("none", npb.NP_GRAN_NONE, {}), ("warp", npb.NP_GRAN_WARP, {}), ("block", npb.NP_GRAN_BLOCK, {}),
+             ("mb1", npb.NP_GRAN_MULTIBLOCK, {"group_blocks": 1}),
+             ("mb3", npb.NP_GRAN_MULTIBLOCK, {"group_blocks": 3}),
+             ("mb8", npb.NP_GRAN_MULTIBLOCK, {"group_blocks": 8}),
+             ("griddev", npb.NP_GRAN_GRID_DEVICE, {}), ("gridhost", npb.NP_GRAN_GRID_HOST, {})]
+    for gname, gran, extra in grans:
+        for T in (0, 1, 32, 128, 1024, npb.INT32_MAX):
+            for cf in (1, 2, 4, 8, 16):
+                out.append((f"{gname}-T{T}-C{cf}",
+                            npb.config("tca", granularity=gran, threshold=T, cfactor=cf, **extra)))
+    return out

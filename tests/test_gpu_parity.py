@@ -1,0 +1,335 @@
+"""GPU parity: every form of the nested-parallel engine against the CPU oracle.
+
+Integer work (BFS levels, SSSP distances, tessellation offsets) must match
+bit for bit; tessellation points must satisfy |g - r| <= 1e-5 * max(|r|, 1)
+against the FP64 oracle (FP32 evaluation of a quadratic with coefficients in
+[0, 1] errs by a few ulp of 1, about 1e-7). Stats are checked where the
+definition of the form fixes them (threshold above every degree: no launch;
+plain CDP: one launch per parent with children).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import DevGraph, bezier, bfs, form_grid, sssp
+from invariants import bezier_tolerance_ok, check_bfs_levels, check_sssp_dist, csr_from_edges
+from paper_2201_02789_gb300 import gen
+from paper_2201_02789_gb300 import nestpar as npb
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2201_02789_gb300 import build as nbuild
+    nbuild.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    c = npb.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def g4k():
+    g = gen.bfs4k()
+    return g, DevGraph(g), oracle.bfs(g.row_ptr, g.col, 0), oracle.sssp(g.row_ptr, g.col, g.w, 0)
+
+
+FORMS = form_grid()
+
+
+@pytest.mark.parametrize("name,cfg", FORMS, ids=[f[0] for f in FORMS])
+def test_bfs_sssp_all_forms_bitexact(ctx, g4k, name, cfg):
+    g, dg, ref_l, ref_d = g4k
+    lv, st = bfs(ctx, dg, 0, cfg, stats=True)
+    np.testing.assert_array_equal(lv, ref_l)
+    d, st2 = sssp(ctx, dg, 0, cfg, stats=True)
+    np.testing.assert_array_equal(d, ref_d)
+    for s in (st, st2):
+        assert s["error"] == 0 and s["launch_failures"] == 0 and s["timeouts"] == 0
+        if cfg.variant == npb.NP_VARIANT_NODP or cfg.threshold == npb.INT32_MAX:
+            assert s["device_launches"] == 0
+    reached = ref_l >= 0
+    assert st["parents"] == reached.sum()
+    assert st["items"] == np.diff(g.row_ptr)[reached].sum()
+    if cfg.variant == npb.NP_VARIANT_CDP and cfg.granularity == npb.NP_GRAN_NONE and cfg.threshold <= 1:
+        has_children = (np.diff(g.row_ptr)[reached] > 0).sum()
+        assert st["launch_parents"] == has_children
+        assert st["device_launches"] == has_children
+
+
+EXTRA = [
+    ("atomic-mb2", dict(granularity="multiblock", group_blocks=2, scan=npb.NP_SCAN_ATOMIC)),
+    ("atomic-griddev", dict(granularity="grid_device", scan=npb.NP_SCAN_ATOMIC)),
+    ("atomic-gridhost", dict(granularity="grid_host", scan=npb.NP_SCAN_ATOMIC, threshold=1)),
+    ("aggthr-warp", dict(granularity="warp", agg_threshold=4, threshold=2)),
+    ("aggthr-block", dict(granularity="block", agg_threshold=16, threshold=2)),
+    ("child32", dict(child_block=32, threshold=1, cfactor=16)),
+    ("child1024", dict(child_block=1024, threshold=1, cfactor=1)),
+    ("parent64", dict(parent_block=64, granularity="multiblock", group_blocks=5)),
+    ("parent512", dict(parent_block=512, granularity="grid_device")),
+    ("grid1", dict(parent_grid=1, granularity="multiblock", group_blocks=2)),
+    ("grid3-host", dict(parent_grid=3, threshold=1)),
+    ("driver-host", dict(driver=npb.NP_DRIVER_HOST, granularity="block")),
+    ("driver-chunk1", dict(driver=npb.NP_DRIVER_CHUNK, unroll=1, granularity="warp")),
+    ("driver-chunk7", dict(driver=npb.NP_DRIVER_CHUNK, unroll=7)),
+    ("driver-while1", dict(driver=npb.NP_DRIVER_WHILE, unroll=1)),
+    ("driver-while16", dict(driver=npb.NP_DRIVER_WHILE, unroll=16, threshold=0)),
+    ("nodp-host", dict(variant=npb.NP_VARIANT_NODP, driver=npb.NP_DRIVER_HOST)),
+]
+
+
+@pytest.mark.parametrize("name,kw", EXTRA, ids=[e[0] for e in EXTRA])
+def test_extra_settings_bitexact(ctx, g4k, name, kw):
+    g, dg, ref_l, ref_d = g4k
+    cfg = npb.config("tca", **kw)
+    lv, st = bfs(ctx, dg, 0, cfg, stats=True)
+    np.testing.assert_array_equal(lv, ref_l)
+    d, st2 = sssp(ctx, dg, 0, cfg, stats=True)
+    np.testing.assert_array_equal(d, ref_d)
+    assert st["error"] == 0 and st2["error"] == 0
+
+
+def test_while_driver_refuses_device_launch_forms(ctx, g4k):
+    _, dg, _, _ = g4k
+    cfg = npb.config("tca", granularity="block", driver=npb.NP_DRIVER_WHILE)
+    level = torch.empty(dg.n, dtype=torch.int32, device="cuda:0")
+    assert npb.np_bfs(ctx.handle, dg.csr, 0, level, cfg, check=False) == npb.NP_ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------------ edge cases
+
+def _graph_from_edges(n, edges, ws=None):
+    if edges:
+        rp, col, w = csr_from_edges(n, edges, ws or [1 + (i * 37) % 255 for i in range(len(edges))])
+    else:
+        rp, col, w = np.zeros(n + 1, np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint32)
+    return gen.Csr(n, rp, col, w)
+
+
+def _edge_graphs():
+    out = {}
+    out["single_vertex"] = _graph_from_edges(1, [])
+    out["isolated_source"] = _graph_from_edges(5, [(1, 2), (2, 3), (3, 4)])
+    # hub with a ragged degree well above a child grid: 70001 children
+    hub = [(0, 1 + i) for i in range(70001)] + [(5, 0), (70001, 2)]
+    out["hub"] = _graph_from_edges(70002, hub)
+    # long path: thousands of levels through the level loop
+    out["path"] = _graph_from_edges(3000, [(i, i + 1) for i in range(2999)])
+    # duplicates and self-loops
+    out["dups"] = _graph_from_edges(6, [(0, 1), (0, 1), (1, 1), (1, 2), (2, 0), (2, 3), (3, 3), (3, 4), (0, 4)])
+    out["road"] = gen.road_grid(60, 70, seed=6)
+    out["rmat12"] = gen.rmat(12, 8, seed=13)
+    return out
+
+
+EDGE = _edge_graphs()
+
+
+@pytest.mark.parametrize("gname", list(EDGE))
+@pytest.mark.parametrize("form", ["nodp", "cdp", "tc", "tca", "mb", "block"])
+def test_edge_graphs(ctx, gname, form):
+    g = EDGE[gname]
+    kw = {"mb": dict(granularity="multiblock", group_blocks=2, threshold=4),
+          "block": dict(granularity="block", threshold=1, cfactor=2)}.get(form, {})
+    cfg = npb.config(form if form in ("nodp", "cdp", "tc", "tca") else "tca", **kw)
+    dg = DevGraph(g)
+    for src in sorted({0, g.n - 1, g.n // 2}):
+        np.testing.assert_array_equal(bfs(ctx, dg, src, cfg), oracle.bfs(g.row_ptr, g.col, src))
+        np.testing.assert_array_equal(sssp(ctx, dg, src, cfg), oracle.sssp(g.row_ptr, g.col, g.w, src))
+
+
+def test_hand_worked_fixture(ctx, tiny_graph):
+    rp, col, w, level, dist = tiny_graph
+    dg = DevGraph(gen.Csr(7, rp, col, w))
+    for form in ("nodp", "cdp", "tca"):
+        np.testing.assert_array_equal(bfs(ctx, dg, 0, npb.config(form)), level)
+        np.testing.assert_array_equal(sssp(ctx, dg, 0, npb.config(form)), dist)
+
+
+def test_invalid_arguments(ctx, g4k):
+    _, dg, _, _ = g4k
+    level = torch.empty(dg.n, dtype=torch.int32, device="cuda:0")
+    cfg = npb.config("tca")
+    assert npb.np_bfs(ctx.handle, dg.csr, -1, level, cfg, check=False) == npb.NP_ERR_INVALID
+    assert npb.np_bfs(ctx.handle, dg.csr, dg.n, level, cfg, check=False) == npb.NP_ERR_INVALID
+    assert npb.np_bfs(ctx.handle, dg.csr, 0, None, cfg, check=False) == npb.NP_ERR_INVALID
+    for bad in (dict(cfactor=3), dict(child_block=48), dict(parent_block=1024), dict(unroll=0),
+                dict(granularity=9), dict(granularity="multiblock", group_blocks=0)):
+        assert npb.np_bfs(ctx.handle, dg.csr, 0, level, cfg.replace(**bad), check=False) == npb.NP_ERR_INVALID
+    nw = npb.make_csr(dg.row_ptr, dg.col, None, n=dg.n, m=dg.m)
+    assert npb.np_sssp(ctx.handle, nw, 0, level, cfg, check=False) == npb.NP_ERR_INVALID
+
+
+def test_repeat_and_context_reuse(ctx, g4k):
+    g, dg, ref_l, ref_d = g4k
+    other = gen.rmat(13, 16, seed=17)
+    dgo = DevGraph(other)
+    ref_o = oracle.sssp(other.row_ptr, other.col, other.w, 3)
+    for _ in range(3):
+        for cfg in (npb.config("tca"), npb.config("cdp"), npb.config("tca", granularity="multiblock")):
+            np.testing.assert_array_equal(bfs(ctx, dg, 0, cfg), ref_l)
+            np.testing.assert_array_equal(sssp(ctx, dgo, 3, cfg), ref_o)
+            np.testing.assert_array_equal(sssp(ctx, dg, 0, cfg), ref_d)
+
+
+# ---------------------------------------------------------------- tessellation
+
+BT_FORMS = [("nodp", {}), ("cdp", {}), ("t", {}), ("tc", {}), ("tca", {}),
+            ("tca", dict(granularity="block")), ("tca", dict(granularity="warp", threshold=8)),
+            ("tca", dict(granularity="multiblock", group_blocks=4, cfactor=2)),
+            ("tca", dict(granularity="grid_device", scan=npb.NP_SCAN_ATOMIC)),
+            ("tca", dict(granularity="grid_host", threshold=0, cfactor=16, child_block=64)),
+            ("tca", dict(threshold=npb.INT32_MAX))]
+
+
+@pytest.mark.parametrize("form,kw", BT_FORMS, ids=[f"{f}-{i}" for i, (f, _) in enumerate(BT_FORMS)])
+def test_bezier_forms(ctx, form, kw):
+    ctrl = gen.bezier_curves(3000, seed=31)
+    ref_off, ref_pts = oracle.bezier(ctrl)
+    status, off, pts, st = bezier(ctx, ctrl, npb.config(form, **kw))
+    assert status == npb.NP_OK
+    np.testing.assert_array_equal(off, ref_off)
+    ok, worst = bezier_tolerance_ok(pts[: ref_off[-1]], ref_pts)
+    assert ok, worst
+    assert st["items"] == ref_off[-1] and st["parents"] == 3000
+
+
+def test_bezier_hand_counts_on_gpu(ctx):
+    from conftest import read_golden
+    rows = read_golden("bezier_counts.txt")["rows"]
+    ctrl = np.array([[float(x) for x in r[:6]] for r in rows], np.float32).reshape(-1, 3, 2)
+    status, off, pts, _ = bezier(ctx, ctrl, npb.config("tca"))
+    assert status == npb.NP_OK
+    np.testing.assert_array_equal(np.diff(off), [int(r[6]) for r in rows])
+
+
+def test_bezier_capacity_and_empty(ctx):
+    ctrl = gen.bezier_curves(200, seed=32)
+    ref_off, ref_pts = oracle.bezier(ctrl)
+    cap = int(ref_off[100])            # room for the first 100 curves only
+    status, off, pts, st = bezier(ctx, ctrl, npb.config("tca"), cap=cap, check=False)
+    assert status == npb.NP_ERR_CAPACITY
+    np.testing.assert_array_equal(off, ref_off)
+    ok, _ = bezier_tolerance_ok(pts[:cap], ref_pts[:cap])
+    assert ok
+    status, off, _, _ = bezier(ctx, np.zeros((0, 3, 2), np.float32), npb.config("tca"))
+    assert status == npb.NP_OK and off[0] == 0
+
+
+# ------------------------------------------------------------ one nesting pass
+
+def test_run_nested_bfs_levels(ctx, g4k):
+    g, dg, ref_l, _ = g4k
+    dev = "cuda:0"
+    level = torch.full((g.n,), -1, dtype=torch.int32, device=dev)
+    level[0] = 0
+    cur = torch.tensor([0], dtype=torch.int32, device=dev)
+    host_level = np.full(g.n, -1, np.int32)
+    host_level[0] = 0
+    host_cur = np.array([0], np.int32)
+    L = 0
+    while host_cur.size:
+        nxt = torch.empty(g.n, dtype=torch.int32, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        body = npb.np_body(kind=npb.NP_BODY_BFS_VISIT, next_level=L + 1, level=level.data_ptr(),
+                           next=nxt.data_ptr(), next_count=cnt.data_ptr())
+        parents = npb.np_parents(cur.data_ptr(), cur.shape[0])
+        cfg = npb.config("tca", granularity=["grid_host", "multiblock", "block", "none"][L % 4], threshold=2)
+        npb.np_run_nested(ctx.handle, parents, npb.NP_COUNT_CSR_DEGREE, dg.csr, body, cfg)
+        got = np.sort(nxt[: int(cnt.item())].cpu().numpy())
+        ref = np.sort(oracle.bfs_expand(g.row_ptr, g.col, host_cur, L, host_level))
+        np.testing.assert_array_equal(got, ref)
+        host_cur, cur, L = ref, nxt[: int(cnt.item())].clone(), L + 1
+    np.testing.assert_array_equal(level.cpu().numpy(), ref_l)
+
+
+def test_run_nested_sssp_pass_sandwich(ctx):
+    """One chaotic relaxation pass lies between the synchronous pass and the
+    final distances, and appends exactly the vertices whose distance dropped."""
+    g = gen.rmat(12, 16, seed=19)
+    dg = DevGraph(g)
+    final = oracle.sssp(g.row_ptr, g.col, g.w, 0)
+    rng = np.random.default_rng(4)
+    dist0 = final.astype(np.int64) + rng.integers(0, 40, g.n)
+    dist0 = np.where(final == 0xFFFFFFFF, 0xFFFFFFFF, dist0).astype(np.uint32)
+    dist0[0] = 0
+    frontier = np.nonzero(dist0 != 0xFFFFFFFF)[0].astype(np.int32)[::3].copy()
+    dev = "cuda:0"
+    d_dist = torch.from_numpy(dist0.view(np.int32).copy()).to(dev)
+    stamp = torch.full((g.n,), -1, dtype=torch.int32, device=dev)
+    nxt = torch.empty(g.n, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    fr = torch.from_numpy(frontier).to(dev)
+    body = npb.np_body(kind=npb.NP_BODY_SSSP_RELAX, iteration=1, dist=d_dist.data_ptr(), stamp=stamp.data_ptr(),
+                       next=nxt.data_ptr(), next_count=cnt.data_ptr())
+    npb.np_run_nested(ctx.handle, npb.np_parents(fr.data_ptr(), len(frontier)), npb.NP_COUNT_CSR_DEGREE, dg.csr,
+                      body, npb.config("tca", threshold=8))
+    got = d_dist.cpu().numpy().view(np.uint32)
+    sync = oracle.sssp_relax_pass(g.row_ptr, g.col, g.w, frontier, dist0)
+    assert np.all(got <= sync) and np.all(got >= final)
+    pushed = np.sort(nxt[: int(cnt.item())].cpu().numpy())
+    np.testing.assert_array_equal(pushed, np.nonzero(got < dist0)[0])
+
+
+def test_run_nested_bezier_subset(ctx):
+    ctrl = gen.bezier_curves(1000, seed=33)
+    ids = np.arange(999, -1, -7, dtype=np.int32)       # reversed, strided subset
+    ref_counts = np.array([oracle.bezier_count(ctrl[i]) for i in ids])
+    dev = "cuda:0"
+    c_d = torch.from_numpy(ctrl).to(dev)
+    off = torch.empty(len(ids) + 1, dtype=torch.int32, device=dev)
+    cap = int(ref_counts.sum())
+    pts = torch.empty((cap, 2), dtype=torch.float32, device=dev)
+    idt = torch.from_numpy(ids).to(dev)
+    body = npb.np_body(kind=npb.NP_BODY_BEZIER_EVAL, ctrl=c_d.data_ptr(), offsets=off.data_ptr(),
+                       points=pts.data_ptr(), cap=cap)
+    npb.np_run_nested(ctx.handle, npb.np_parents(idt.data_ptr(), len(ids)), npb.NP_COUNT_BEZIER, None, body,
+                      npb.config("tca", threshold=64))
+    o = off.cpu().numpy()
+    np.testing.assert_array_equal(np.diff(o), ref_counts)
+    p = pts.cpu().numpy()
+    for k in range(0, len(ids), 11):
+        N = ref_counts[k]
+        for j in (0, N // 2, N - 1):
+            ref = oracle.bezier_point(ctrl[ids[k]], N, j)
+            assert bezier_tolerance_ok(p[o[k] + j], ref)[0]
+
+
+# ------------------------------------------------------------ full-size configs
+
+@pytest.fixture(scope="module")
+def rmat20():
+    g = gen.rmat20()
+    return g, DevGraph(g)
+
+
+@pytest.mark.parametrize("form", ["tca", "nodp", "tca-mb", "tca-atomic"])
+def test_rmat20_sssp_bfs_full(ctx, rmat20, form):
+    g, dg = rmat20
+    kw = {"tca-mb": dict(granularity="multiblock", group_blocks=8),
+          "tca-atomic": dict(scan=npb.NP_SCAN_ATOMIC)}.get(form, {})
+    cfg = npb.config(form.split("-")[0], **kw)
+    ref_l = oracle.bfs(g.row_ptr, g.col, 0)
+    np.testing.assert_array_equal(bfs(ctx, dg, 0, cfg), ref_l)
+    d, st = sssp(ctx, dg, 0, cfg, stats=True)
+    np.testing.assert_array_equal(d, oracle.sssp(g.row_ptr, g.col, g.w, 0))
+    assert st["error"] == 0
+
+
+def test_rmat20_plain_cdp_full(ctx, rmat20):
+    g, dg = rmat20
+    lv, st = bfs(ctx, dg, 0, npb.config("cdp"), stats=True)
+    np.testing.assert_array_equal(lv, oracle.bfs(g.row_ptr, g.col, 0))
+    assert st["device_launches"] + st["launch_failures"] == st["launch_parents"]
+
+
+def test_bt64k_full(ctx):
+    ctrl = gen.bt64k()
+    ref_off, ref_pts = oracle.bezier(ctrl)
+    status, off, pts, st = bezier(ctx, ctrl, npb.config("tca"), cap=int(ref_off[-1]))
+    assert status == npb.NP_OK
+    np.testing.assert_array_equal(off, ref_off)
+    ok, worst = bezier_tolerance_ok(pts, ref_pts)
+    assert ok, worst
