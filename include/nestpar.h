@@ -126,6 +126,8 @@ typedef struct np_stats {     /* device-side counters of the last call */
   uint64_t pushes;            /* vertices appended to frontiers */
   uint64_t launch_failures;   /* refused device launches (serialised instead) */
   uint64_t timeouts;          /* expired bounded waits */
+  uint64_t child_items;       /* of `items`, those run by child grids (not serialised) */
+  uint64_t graph_iterations;  /* conditional-while body iterations (while driver) */
   uint32_t error;             /* device error bits: 1 launch, 2 timeout, 4 capacity */
   uint32_t reserved;
 } np_stats;
@@ -215,6 +217,26 @@ np_status np_bfs_host(np_ctx *ctx, int32_t n, int64_t m, const int32_t *row_ptr_
 np_status np_sssp_host(np_ctx *ctx, int32_t n, int64_t m, const int32_t *row_ptr_host,
                        const int32_t *col_idx_host, const uint32_t *weights_host, int32_t src,
                        uint32_t *dist_host, const np_config *cfg, void *stream, np_stats *stats);
+
+/* ---- execution-time breakdown (the paper's Section VII-B, measured instead of
+ *      obtained by deactivating code) ---- */
+typedef struct np_profile {
+  double parent_ms;           /* summed CUDA-event time of parent-grid launches */
+  double child_ms;            /* summed time of stream-ordered child grids (grid-host form) */
+  double other_ms;            /* init and level-advance kernels */
+  int64_t parent_launches;
+  int64_t child_launches;
+  int64_t other_launches;
+} np_profile;
+
+/* While enabled (on != 0), np_bfs / np_sssp / np_bezier / np_run_nested launch
+ * every kernel of the path separately on the caller's stream (no graphs),
+ * bracket each with CUDA events and wait after each level; the grids and
+ * kernels are the ones the graph drivers run. Device-side (child) launches are
+ * included in their parent grid's time. */
+np_status np_profile_enable(np_ctx *ctx, int32_t on);
+/* Accumulated times since the last reset; reset != 0 clears them. */
+np_status np_profile_read(np_ctx *ctx, np_profile *out, int32_t reset);
 
 const char *np_status_string(np_status s);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */

@@ -60,6 +60,7 @@ __global__ void init_solve_kernel(LevelState* st, int kind, int n, int src, int*
 
 __global__ void init_fixed_kernel(LevelState* st) {
   st->epoch += 1;
+  st->body_iters = 0;
   st->ticket = 0;
   st->parent_done = 0;
   st->child_done = 0;
@@ -171,6 +172,10 @@ struct np_ctx {
   // device staging for the *_host entry points
   unsigned char* stage = nullptr;
   size_t stage_bytes = 0;
+  // execution-time breakdown (np_profile_*)
+  bool profile = false;
+  np_profile prof{};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::mutex mu;
 };
 
@@ -336,6 +341,55 @@ np_status enqueue_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool le
   return NP_OK;
 }
 
+// Profile mode: the grids of one level (or pass) launched one by one between
+// CUDA events, then waited for; times go to the context's breakdown.
+np_status profiled_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool level_mode, cudaStream_t s) {
+  a.advance = (level_mode && p.mode == M_NODP) ? 1 : 0;
+  void* pargs[] = {&a};
+  NP_CK(cudaEventRecord(c->ev[0], s));
+  NP_CK(cudaLaunchKernel(p.parent, dim3(g.pgrid), dim3(g.pblock), pargs, 0, s));
+  NP_CK(cudaEventRecord(c->ev[1], s));
+  bool child = false, other = false;
+  if (p.mode == M_GRID_HOST) {
+    AggSeg seg{};
+    seg.rec = a.rec;
+    seg.boff = a.boff;
+    seg.mode = a.scan == 0 ? 1 : 2;
+    seg.advance = level_mode ? 1 : 0;
+    seg.level_mode = level_mode ? 1 : 0;
+    seg.fr0 = a.fr0;
+    seg.fr1 = a.fr1;
+    BodyArgs b = a.b;
+    if (!level_mode) {
+      b.L = a.L_fixed;
+      b.next = a.next_ovr;
+      b.next_count = a.next_count_ovr;
+    }
+    void* cargs[] = {&b, &seg};
+    NP_CK(cudaLaunchKernel(p.child, dim3(g.cgrid), dim3(g.cblock), cargs, 0, s));
+    child = true;
+  } else if (p.mode == M_DEVICE_LAUNCH && level_mode) {
+    advance_kernel<<<1, 1, 0, s>>>(c->st);
+    NP_CK(cudaGetLastError());
+    other = true;
+  }
+  NP_CK(cudaEventRecord(c->ev[2], s));
+  NP_CK(cudaEventSynchronize(c->ev[2]));
+  float t01 = 0.f, t12 = 0.f;
+  NP_CK(cudaEventElapsedTime(&t01, c->ev[0], c->ev[1]));
+  NP_CK(cudaEventElapsedTime(&t12, c->ev[1], c->ev[2]));
+  c->prof.parent_ms += t01;
+  c->prof.parent_launches += 1;
+  if (child) {
+    c->prof.child_ms += t12;
+    c->prof.child_launches += 1;
+  } else if (other) {
+    c->prof.other_ms += t12;
+    c->prof.other_launches += 1;
+  }
+  return NP_OK;
+}
+
 std::string graph_key(const char* tag, const Plan& p, const Args& a, const Grids& g, int unroll) {
   std::string k(tag);
   k.append(reinterpret_cast<const char*>(&p), sizeof(p));
@@ -452,6 +506,8 @@ np_status finish(np_ctx* c, cudaStream_t s, np_stats* stats) {
   stats->pushes = h.s[S_PUSHES];
   stats->launch_failures = h.s[S_LFAIL];
   stats->timeouts = h.s[S_TIMEOUT];
+  stats->child_items = h.s[S_CITEMS];
+  stats->graph_iterations = (uint64_t)h.body_iters;
   stats->error = h.error;
   if (h.error) {
     NP_CK(cudaMemsetAsync(&c->st->error, 0, sizeof(unsigned), s));
@@ -467,6 +523,18 @@ np_status run_levels(np_ctx* c, const Plan& p, const Args& a, const np_config& c
   if (driver == NP_DRIVER_AUTO) driver = p.mode == M_DEVICE_LAUNCH ? NP_DRIVER_CHUNK : NP_DRIVER_WHILE;
   if (driver == NP_DRIVER_WHILE && p.mode == M_DEVICE_LAUNCH) return NP_ERR_UNSUPPORTED;
   const int max_levels = n + 2;
+  if (c->profile) {
+    for (int iter = 0;; iter++) {
+      if (iter > max_levels + 16) return NP_ERR_TIMEOUT;
+      np_status st = profiled_pass(c, p, a, g, true, s);
+      if (st != NP_OK) return st;
+      int level = 0, count = 0;
+      st = read_header(c, s, &level, &count);
+      if (st != NP_OK) return st;
+      if (count <= 0 || level >= max_levels) break;
+    }
+    return NP_OK;
+  }
   if (driver == NP_DRIVER_WHILE) {
     cudaGraphExec_t exec;
     np_status st = while_graph(c, p, a, g, cfg.unroll, &exec);
@@ -526,8 +594,17 @@ np_status solve(np_ctx* c, int kind, const np_csr* g, int src, int* level, unsig
   a.b.dist = dist;
   a.b.stamp = wsp<int>(c, c->lay.off_stamp);
   const int blocks = (int)((g->n + 255) / 256 < 4096 ? (g->n + 255) / 256 : 4096);
+  if (c->profile) NP_CK(cudaEventRecord(c->ev[0], s));
   init_solve_kernel<<<blocks, 256, 0, s>>>(c->st, kind, g->n, src, level, dist, a.b.stamp, a.fr0, g->n + 2);
   NP_CK(cudaGetLastError());
+  if (c->profile) {
+    NP_CK(cudaEventRecord(c->ev[3], s));
+    NP_CK(cudaEventSynchronize(c->ev[3]));
+    float t = 0.f;
+    NP_CK(cudaEventElapsedTime(&t, c->ev[0], c->ev[3]));
+    c->prof.other_ms += t;
+    c->prof.other_launches += 1;
+  }
   st = run_levels(c, p, a, *cfg, g->n, s);
   if (st != NP_OK) return st;
   return finish(c, s, stats);
@@ -539,6 +616,18 @@ np_status fixed_pass(np_ctx* c, const Args& a0, const np_config& cfg, const Body
   Plan p = make_plan(K, cfg);
   Args a = a0;
   Grids g = grids_for(c, p, cfg, count);
+  if (c->profile) {
+    NP_CK(cudaEventRecord(c->ev[0], s));
+    init_fixed_kernel<<<1, 1, 0, s>>>(c->st);
+    NP_CK(cudaGetLastError());
+    NP_CK(cudaEventRecord(c->ev[3], s));
+    NP_CK(cudaEventSynchronize(c->ev[3]));
+    float t = 0.f;
+    NP_CK(cudaEventElapsedTime(&t, c->ev[0], c->ev[3]));
+    c->prof.other_ms += t;
+    c->prof.other_launches += 1;
+    return profiled_pass(c, p, a, g, false, s);
+  }
   std::string key = graph_key("fixed", p, a, g, 1);
   auto it = c->graphs.find(key);
   cudaGraphExec_t exec = nullptr;
@@ -623,6 +712,7 @@ np_status np_create(np_ctx** out, int32_t device) {
   if (e == cudaSuccess) e = cudaMallocHost(&c->pin, 64);
   if (e == cudaSuccess) e = cudaMallocHost(&c->pin_state, sizeof(LevelState));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  for (int k = 0; k < 4 && e == cudaSuccess; k++) e = cudaEventCreate(&c->ev[k]);
   if (e != cudaSuccess) {
     np_destroy(c);
     return from_cuda(e);
@@ -642,6 +732,8 @@ np_status np_destroy(np_ctx* c) {
   if (c->pin) cudaFreeHost(c->pin);
   if (c->pin_state) cudaFreeHost(c->pin_state);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (int k = 0; k < 4; k++)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   delete c;
   return NP_OK;
 }
@@ -823,6 +915,21 @@ np_status np_sssp_host(np_ctx* c, int32_t n, int64_t m, const int32_t* row_ptr_h
   NP_CK(cudaStreamSynchronize(s));
   np_stats tmp;
   return np_sync(c, stream, stats ? stats : &tmp);
+}
+
+np_status np_profile_enable(np_ctx* c, int32_t on) {
+  if (!c) return NP_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->profile = on != 0;
+  return NP_OK;
+}
+
+np_status np_profile_read(np_ctx* c, np_profile* out, int32_t reset) {
+  if (!c || !out) return NP_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  *out = c->prof;
+  if (reset) c->prof = np_profile{};
+  return NP_OK;
 }
 
 const char* np_status_string(np_status s) {

@@ -34,7 +34,7 @@ constexpr unsigned kFull = 0xffffffffu;
 enum Gran : int { G_NONE = 0, G_WARP = 1, G_BLOCK = 2, G_MULTIBLOCK = 3, G_GRID_DEVICE = 4,
                   G_GRID_HOST = 5, G_NODP = 6 };
 enum Stat : int { S_LEVELS, S_PARENTS, S_SERIAL, S_LAUNCHP, S_DEVLAUNCH, S_AGGGRID, S_CBLOCKS,
-                  S_ITEMS, S_PUSHES, S_LFAIL, S_TIMEOUT, S_N };
+                  S_ITEMS, S_PUSHES, S_LFAIL, S_TIMEOUT, S_CITEMS, S_N };
 
 // Device-resident state of one solve. Level L reads frontier buffer L&1 with
 // count[L%3] and appends to buffer (L+1)&1 / count[(L+1)%3]; the parent
@@ -616,7 +616,10 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
         atomicAdd(&s_stat[S_SERIAL], 1u);
         run_serial<Body>(b, pid, base, N);
       }
-      if (launch) atomicAdd(&s_stat[S_LAUNCHP], 1u);
+      if (launch) {
+        atomicAdd(&s_stat[S_LAUNCHP], 1u);
+        atomicAdd(&s_stat[S_CITEMS], (unsigned)N);
+      }
       const unsigned cg = launch ? (unsigned)ceil_div(ceil_div(N, CB), a.cfactor) : 0u;
       if constexpr (GRAN == G_NONE) {
         if (launch) launch_direct<Body, CF>(b, pid, base, N, CB, s_stat);

@@ -67,11 +67,21 @@ class np_csr(ctypes.Structure):
 class np_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in
                 ("levels", "parents", "serial_parents", "launch_parents", "device_launches",
-                 "aggregated_grids", "child_blocks", "items", "pushes", "launch_failures", "timeouts")] + \
+                 "aggregated_grids", "child_blocks", "items", "pushes", "launch_failures", "timeouts",
+                 "child_items", "graph_iterations")] + \
                [("error", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
+
+
+class np_profile(ctypes.Structure):
+    _fields_ = [("parent_ms", ctypes.c_double), ("child_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
+                ("parent_launches", ctypes.c_int64), ("child_launches", ctypes.c_int64),
+                ("other_launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class np_parents(ctypes.Structure):
@@ -104,6 +114,8 @@ _SIGS = {
                     ctypes.POINTER(np_stats)],
     "np_sssp_host": [_VP, _I32, _I64, _VP, _VP, _VP, _I32, _VP, ctypes.POINTER(np_config), _VP,
                      ctypes.POINTER(np_stats)],
+    "np_profile_enable": [_VP, _I32],
+    "np_profile_read": [_VP, ctypes.POINTER(np_profile), _I32],
     "np_status_string": [_I32],
     "np_version": [],
 }
@@ -272,6 +284,16 @@ def np_sssp_host(ctx, row_ptr, col_idx, weights, src: int, dist_out, cfg=None, s
                            ctypes.byref(st) if want else None)
     _check(s, "np_sssp_host", check)
     return (s, st.as_dict()) if want else s
+
+
+def np_profile_enable(ctx, on: bool = True) -> int:
+    return _check(lib().np_profile_enable(ctx, 1 if on else 0), "np_profile_enable", True)
+
+
+def np_profile_read(ctx, reset: bool = False) -> dict:
+    p = np_profile()
+    _check(lib().np_profile_read(ctx, ctypes.byref(p), 1 if reset else 0), "np_profile_read", True)
+    return p.as_dict()
 
 
 # ------------------------------------------------------------ configurations
