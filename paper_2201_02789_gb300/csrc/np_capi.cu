@@ -765,7 +765,8 @@ np_status np_sssp(np_ctx* c, const np_csr* g, int32_t src, uint32_t* dist, const
 
 np_status np_bezier(np_ctx* c, const float* ctrl, int32_t ncurves, int32_t* offsets, float* points, int64_t cap,
                     const np_config* cfg, void* stream, np_stats* stats) {
-  if (!c || !ctrl || !offsets || ncurves < 0 || cap < 0 || (cap > 0 && !points)) return NP_ERR_INVALID;
+  if (!c || (ncurves > 0 && !ctrl) || !offsets || ncurves < 0 || cap < 0 || (cap > 0 && !points))
+    return NP_ERR_INVALID;
   np_status st = check_config(cfg);
   if (st != NP_OK) return st;
   if (ncurves == 0) {
