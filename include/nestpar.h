@@ -175,6 +175,36 @@ np_status np_bezier(np_ctx *ctx, const float *ctrl, int32_t ncurves, int32_t *of
                     float *points, int64_t cap, const np_config *cfg, void *stream,
                     np_stats *stats);
 
+/* ---- allocation-free tessellation (the paper has no counterpart) ----
+ * Some callers cannot allocate device memory at the time they call this
+ * library: code recording its GPU work into a CUDA graph by stream capture
+ * (an allocation is not a capturable operation), programs whose device
+ * memory all belongs to their own pool allocator or to a budget fixed at
+ * start-up, and latency-critical loops where an allocation may wait for the
+ * device. np_bezier_noalloc serves them: the same tessellation as np_bezier
+ * (same kernels, same results), with no context and no allocation of any
+ * kind. Its scratch (level state, aggregation records, look-back tile states)
+ * is one static device array of about 1.5 MB inside the library, sized for
+ * NP_NOALLOC_MAX_CURVES curves; every GPU that loads the library holds it
+ * until the process exits.
+ *   - ncurves > NP_NOALLOC_MAX_CURVES is rejected with NP_ERR_INVALID before
+ *     anything is enqueued; so are the argument errors of np_bezier.
+ *   - Only forms without device-side launches run here: NP_VARIANT_NODP, or
+ *     NP_VARIANT_CDP with NP_GRAN_GRID_HOST; other forms get NP_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's device address and
+ *     clears the array with an asynchronous memset on `stream`; make that
+ *     first call before any stream capture.
+ *   - All calls share the array, which keeps the last call's contents; each
+ *     call resets what must start at zero. Calls that overlap on the GPU (on
+ *     different streams, or from several host threads) race on the array and
+ *     must be serialised by the caller.
+ *   - The call only enqueues work on `stream`; it reports no device-side
+ *     status and no stats. A capacity shortfall shows as
+ *     offsets[ncurves] > cap (curves that do not fit are skipped). */
+#define NP_NOALLOC_MAX_CURVES 65536
+np_status np_bezier_noalloc(const float *ctrl, int32_t ncurves, int32_t *offsets, float *points,
+                            int64_t cap, const np_config *cfg, void *stream);
+
 /* ---- one nesting pass over an explicit parent set (Section II-A) ---- */
 #define NP_COUNT_CSR_DEGREE 0   /* N = row_ptr[p+1] - row_ptr[p], child i -> edge row_ptr[p] + i */
 #define NP_COUNT_BEZIER 1       /* N = the tessellation point count of curve p */

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libnestpar.so")
-SOURCES = ["np_capi.cu", "np_bfs.cu", "np_sssp.cu", "np_bezier.cu"]
+SOURCES = ["np_capi.cu", "np_bfs.cu", "np_sssp.cu", "np_bezier.cu", "np_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-rdc=true", "-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -114,6 +114,7 @@ _SIGS = {
                     ctypes.POINTER(np_stats)],
     "np_sssp_host": [_VP, _I32, _I64, _VP, _VP, _VP, _I32, _VP, ctypes.POINTER(np_config), _VP,
                      ctypes.POINTER(np_stats)],
+    "np_bezier_noalloc": [_VP, _I32, _VP, _VP, _I64, ctypes.POINTER(np_config), _VP],
     "np_profile_enable": [_VP, _I32],
     "np_profile_read": [_VP, ctypes.POINTER(np_profile), _I32],
     "np_status_string": [_I32],
@@ -254,6 +255,21 @@ def np_bezier(ctx, ctrl, ncurves: int, offsets, points, cap: int, cfg=None, stre
                         ctypes.byref(_cfg(cfg)), _stream(stream), ctypes.byref(st) if want else None)
     _check(s, "np_bezier", check)
     return (s, st.as_dict()) if want else s
+
+
+NP_NOALLOC_MAX_CURVES = 65536
+
+
+def np_bezier_noalloc(ctrl, ncurves: int, offsets, points, cap: int, cfg=None, stream=None,
+                      check: bool = True) -> int:
+    """Tessellation without a context and without any allocation, for callers that
+    cannot allocate device memory when they call (for example while a CUDA graph is
+    being captured). Scratch is a static device array sized for NP_NOALLOC_MAX_CURVES
+    curves; calls that overlap on the GPU race on it. Make the first call on a device
+    before any stream capture (it looks up and clears that array)."""
+    s = lib().np_bezier_noalloc(_ptr(ctrl), int(ncurves), _ptr(offsets), _ptr(points), int(cap),
+                                ctypes.byref(_cfg(cfg)), _stream(stream))
+    return _check(s, "np_bezier_noalloc", check)
 
 
 def np_run_nested(ctx, parents: np_parents, count_kind: int, g: np_csr | None, body: np_body, cfg=None,
