@@ -370,7 +370,8 @@ def run_ours(args, ws, rank, local):
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": CONFIG,
-            "form": "threshold 128 + coarsening 8 + grid aggregation (look-back scan), while-graph level loop",
+            "form": "threshold 32 + coarsening 8 (32-thread child blocks) + grid aggregation (look-back scan), "
+                    "while-graph level loop",
             "ms_per_solve": {"median": statistics.median(ms), "min": min(ms)},
             "edges_reached": mr, "levels": st["levels"], "relaxations": st["items"],
             "speedup_vs_plain_cdp": forms["plain_cdp"]["ms_per_solve"] / statistics.median(ms),

@@ -101,8 +101,10 @@ typedef struct np_config {
   int32_t reserved[4];   /* must be zero */
 } np_config;
 
-/* Fills the library defaults: CDP, threshold 128, cfactor 8, grid-host
- * aggregation, look-back scan, child block 256, parent block 256, AUTO driver. */
+/* Fills the library defaults: CDP, threshold 32, cfactor 8, grid-host
+ * aggregation, look-back scan, child block 32, parent block 256, AUTO driver
+ * (the best of a threshold x cfactor x child-block sweep of BFS and SSSP on an
+ * R-MAT scale-20 graph on GB300). */
 np_status np_config_default(np_config *cfg);
 
 /* ---- problem descriptions ---- */
@@ -250,6 +252,7 @@ np_status np_sssp_host(np_ctx *ctx, int32_t n, int64_t m, const int32_t *row_ptr
 
 /* ---- execution-time breakdown (the paper's Section VII-B, measured instead of
  *      obtained by deactivating code) ---- */
+#define NP_PROFILE_LEVELS 64
 typedef struct np_profile {
   double parent_ms;           /* summed CUDA-event time of parent-grid launches */
   double child_ms;            /* summed time of stream-ordered child grids (grid-host form) */
@@ -257,6 +260,14 @@ typedef struct np_profile {
   int64_t parent_launches;
   int64_t child_launches;
   int64_t other_launches;
+  /* per level of the last profiled np_bfs / np_sssp call (first NP_PROFILE_LEVELS
+   * levels); the longest level is the paper's "longest iteration" figure */
+  double longest_level_ms;
+  int32_t levels;
+  int32_t reserved;
+  int32_t level_parents[NP_PROFILE_LEVELS];   /* frontier size of each level */
+  double level_parent_ms[NP_PROFILE_LEVELS];
+  double level_child_ms[NP_PROFILE_LEVELS];
 } np_profile;
 
 /* While enabled (on != 0), np_bfs / np_sssp / np_bezier / np_run_nested launch

@@ -28,6 +28,8 @@ namespace {
 
 constexpr int kVersion = 10000;  // 1.0.0
 constexpr size_t kAlign = 256;
+constexpr int kQueueChunk = 32;    // frontier slots a child warp reserves at a time (level mode)
+constexpr int kMaxWarpsPerSM = 64;
 
 __global__ void init_solve_kernel(LevelState* st, int kind, int n, int src, int* level, unsigned* dist,
                                   int* stamp, int* fr0, int max_levels) {
@@ -108,18 +110,21 @@ struct Layout {
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-Layout layout_for(int64_t parents) {
+// Frontier buffers hold up to `parents` appends plus the padding of the
+// warp-private runs of the persistent child grid (at most kQueueChunk per warp).
+Layout layout_for(int64_t parents, int sms) {
   Layout L{};
   L.P2 = ((parents + 1023) / 1024) * 1024 + 1024;
   L.T = L.P2 / 32 + 64;
+  const int64_t fr = L.P2 + (int64_t)(sms > 0 ? sms : 256) * kMaxWarpsPerSM * kQueueChunk;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t r = o;
     o = align_up(o + bytes);
     return r;
   };
-  L.off_fr0 = take(sizeof(int) * L.P2);
-  L.off_fr1 = take(sizeof(int) * L.P2);
+  L.off_fr0 = take(sizeof(int) * fr);
+  L.off_fr1 = take(sizeof(int) * fr);
   L.off_stamp = take(sizeof(int) * L.P2);
   L.off_rec = take(sizeof(int4) * L.P2);
   L.off_boff = take(sizeof(int) * L.P2);
@@ -175,6 +180,7 @@ struct np_ctx {
   // execution-time breakdown (np_profile_*)
   bool profile = false;
   np_profile prof{};
+  int prof_next_parents = 0;   // frontier size of the level about to be profiled
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::mutex mu;
 };
@@ -192,7 +198,7 @@ void drop_graphs(np_ctx* c) {
 np_status ensure_workspace(np_ctx* c, int64_t parents) {
   if (parents <= c->cap_parents && c->ws) return NP_OK;
   int64_t want = parents < 4096 ? 4096 : parents;
-  Layout L = layout_for(want);
+  Layout L = layout_for(want, c->sms);
   drop_graphs(c);
   if (c->ws) {
     NP_CK(cudaDeviceSynchronize());
@@ -296,7 +302,7 @@ void base_args(np_ctx* c, const np_config& cfg, Args& a) {
 }
 
 struct Grids {
-  int pgrid, pblock, cgrid, cblock;
+  int pgrid, pblock, cgrid, cblock, cthreads;
 };
 
 Grids grids_for(np_ctx* c, const Plan& p, const np_config& cfg, int64_t max_parents) {
@@ -308,7 +314,9 @@ Grids grids_for(np_ctx* c, const Plan& p, const np_config& cfg, int64_t max_pare
   int64_t pg = cfg.parent_grid > 0 ? cfg.parent_grid : (int64_t)occupancy(c, p.parent, g.pblock) * c->sms;
   if (pg > tiles) pg = tiles;
   g.pgrid = (int)pg;
-  g.cgrid = p.child ? occupancy(c, p.child, g.cblock) * c->sms : 0;
+  // the persistent child grid hosts cb-thread child blocks in CTAs of at least 256 threads
+  g.cthreads = g.cblock < 256 ? 256 : g.cblock;
+  g.cgrid = p.child ? occupancy(c, p.child, g.cthreads) * c->sms : 0;
   return g;
 }
 
@@ -326,6 +334,8 @@ np_status enqueue_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool le
     seg.level_mode = level_mode ? 1 : 0;
     seg.fr0 = a.fr0;
     seg.fr1 = a.fr1;
+    seg.cb = g.cblock;
+    seg.qchunk = level_mode ? kQueueChunk : 0;
     BodyArgs b = a.b;
     if (!level_mode) {
       b.L = a.L_fixed;
@@ -333,7 +343,7 @@ np_status enqueue_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool le
       b.next_count = a.next_count_ovr;
     }
     void* cargs[] = {&b, &seg};
-    NP_CK(cudaLaunchKernel(p.child, dim3(g.cgrid), dim3(g.cblock), cargs, 0, s));
+    NP_CK(cudaLaunchKernel(p.child, dim3(g.cgrid), dim3(g.cthreads), cargs, 0, s));
   } else if (p.mode == M_DEVICE_LAUNCH && level_mode) {
     advance_kernel<<<1, 1, 0, s>>>(c->st);
     NP_CK(cudaGetLastError());
@@ -359,6 +369,8 @@ np_status profiled_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool l
     seg.level_mode = level_mode ? 1 : 0;
     seg.fr0 = a.fr0;
     seg.fr1 = a.fr1;
+    seg.cb = g.cblock;
+    seg.qchunk = level_mode ? kQueueChunk : 0;
     BodyArgs b = a.b;
     if (!level_mode) {
       b.L = a.L_fixed;
@@ -366,7 +378,7 @@ np_status profiled_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool l
       b.next_count = a.next_count_ovr;
     }
     void* cargs[] = {&b, &seg};
-    NP_CK(cudaLaunchKernel(p.child, dim3(g.cgrid), dim3(g.cblock), cargs, 0, s));
+    NP_CK(cudaLaunchKernel(p.child, dim3(g.cgrid), dim3(g.cthreads), cargs, 0, s));
     child = true;
   } else if (p.mode == M_DEVICE_LAUNCH && level_mode) {
     advance_kernel<<<1, 1, 0, s>>>(c->st);
@@ -386,6 +398,17 @@ np_status profiled_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool l
   } else if (other) {
     c->prof.other_ms += t12;
     c->prof.other_launches += 1;
+  }
+  if (level_mode) {
+    const int k = c->prof.levels;
+    const double lvl = (double)t01 + (child ? (double)t12 : 0.0);
+    if (lvl > c->prof.longest_level_ms) c->prof.longest_level_ms = lvl;
+    if (k < NP_PROFILE_LEVELS) {
+      c->prof.level_parents[k] = c->prof_next_parents;
+      c->prof.level_parent_ms[k] = t01;
+      c->prof.level_child_ms[k] = child ? t12 : 0.0;
+      c->prof.levels = k + 1;
+    }
   }
   return NP_OK;
 }
@@ -524,6 +547,10 @@ np_status run_levels(np_ctx* c, const Plan& p, const Args& a, const np_config& c
   if (driver == NP_DRIVER_WHILE && p.mode == M_DEVICE_LAUNCH) return NP_ERR_UNSUPPORTED;
   const int max_levels = n + 2;
   if (c->profile) {
+    // per-level records describe this call only
+    c->prof.levels = 0;
+    c->prof.longest_level_ms = 0.0;
+    c->prof_next_parents = 1;
     for (int iter = 0;; iter++) {
       if (iter > max_levels + 16) return NP_ERR_TIMEOUT;
       np_status st = profiled_pass(c, p, a, g, true, s);
@@ -531,6 +558,7 @@ np_status run_levels(np_ctx* c, const Plan& p, const Args& a, const np_config& c
       int level = 0, count = 0;
       st = read_header(c, s, &level, &count);
       if (st != NP_OK) return st;
+      c->prof_next_parents = count;
       if (count <= 0 || level >= max_levels) break;
     }
     return NP_OK;
@@ -675,12 +703,12 @@ np_status np_config_default(np_config* cfg) {
   if (!cfg) return NP_ERR_INVALID;
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->variant = NP_VARIANT_CDP;
-  cfg->threshold = 128;
+  cfg->threshold = 32;
   cfg->cfactor = 8;
   cfg->granularity = NP_GRAN_GRID_HOST;
   cfg->group_blocks = 8;
   cfg->agg_threshold = 0;
-  cfg->child_block = 256;
+  cfg->child_block = 32;
   cfg->parent_block = 256;
   cfg->scan = NP_SCAN_LOOKBACK;
   cfg->driver = NP_DRIVER_AUTO;
@@ -741,7 +769,7 @@ np_status np_destroy(np_ctx* c) {
 np_status np_workspace_size(int64_t max_parents, const np_config* cfg, size_t* bytes) {
   if (!bytes || max_parents < 0) return NP_ERR_INVALID;
   if (cfg && check_config(cfg) != NP_OK) return NP_ERR_INVALID;
-  *bytes = layout_for(max_parents < 4096 ? 4096 : max_parents).total + sizeof(LevelState);
+  *bytes = layout_for(max_parents < 4096 ? 4096 : max_parents, 0).total + sizeof(LevelState);
   return NP_OK;
 }
 

@@ -116,6 +116,8 @@ struct AggSeg {
   int mode;                      // 0: fixed segment; 1: grid-host, look-back totals; 2: grid-host, atomic totals
   int advance;                   // 1: the child grid's last CTA advances the level
   int level_mode;                // 1: take L, next and next_count from the level state
+  int cb;                        // child block size; a CTA hosts blockDim.x / cb child blocks
+  int qchunk;                    // frontier slots a warp reserves at a time (0 = exact appends)
   int pad;
 };
 
@@ -255,45 +257,141 @@ __device__ __forceinline__ void block_scan2(unsigned a, unsigned b, unsigned& ea
 }
 
 // Largest j in [lo, hi) with boff[j] <= B, for strictly increasing boff and
-// boff[lo] <= B. k-ary search with k = blockDim.x: every round each thread
-// tests one sample and __syncthreads_count ranks B among them.
-__device__ __forceinline__ int disaggregate(const int* boff, int lo, int hi, int B) {
-  const int T = blockDim.x, tid = threadIdx.x;
-  while (hi - lo > T) {
-    const int stride = ceil_div(hi - lo, T);
-    const int idx = lo + tid * stride;
+// boff[lo] <= B: a 32-ary search run by one warp (one probe per lane and one
+// ballot per round, no block barrier), every lane returns j. Each warp of a
+// child block runs it on its own, so the block never waits on itself.
+__device__ __forceinline__ int warp_search(const int* boff, int lo, int hi, int B) {
+  const int lane = threadIdx.x & 31;
+  while (hi - lo > 32) {
+    const int stride = ceil_div(hi - lo, 32);
+    const int idx = lo + lane * stride;
     const bool p = idx < hi && __ldcg(&boff[idx]) <= B;
-    const int c = max(__syncthreads_count(p), 1);   // >= 1 by the precondition; clamped to stay in range
+    const int c = max(__popc(__ballot_sync(kFull, p)), 1);   // >= 1 by the precondition; clamped to stay in range
     lo += (c - 1) * stride;
     hi = min(hi, lo + stride);
   }
-  const int idx = lo + tid;
+  const int idx = lo + lane;
   const bool p = idx < hi && __ldcg(&boff[idx]) <= B;
-  const int c = max(__syncthreads_count(p), 1);
-  return lo + c - 1;
+  return lo + max(__popc(__ballot_sync(kFull, p)), 1) - 1;
 }
 
-// Append v to the next frontier when pred holds; one atomic per warp.
-// kFullWarp: all 32 lanes are known to be here (child blocks); otherwise the
-// currently active lanes cooperate (serial loops in diverged parent threads).
-template <bool kFullWarp>
-__device__ __forceinline__ void push_frontier(bool pred, int v, int* next, int* next_count) {
-  const unsigned act = kFullWarp ? kFull : __activemask();
-  const unsigned m = __ballot_sync(act, pred);
-  if (m == 0u) return;
+// The same search when the answer is usually close to lo (the next parent of
+// a contiguous run of blocks): one 32-entry window first, the full search only
+// when B lies beyond it.
+__device__ __forceinline__ int warp_search_near(const int* boff, int lo, int hi, int B) {
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(m) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(next_count, __popc(m));
-  base = __shfl_sync(act, base, leader);
-  if (pred) next[base + __popc(m & lanemask_lt())] = v;
+  const int idx = lo + lane;
+  const bool p = idx < hi && __ldcg(&boff[idx]) <= B;
+  const int c = __popc(__ballot_sync(kFull, p));
+  if (c < 32 || lo + 32 >= hi) return lo + max(c, 1) - 1;
+  return warp_search(boff, lo + 31, hi, B);
 }
+
+// ------------------------------------------------------------ frontier sinks
+//
+// Appends to the next frontier go through a sink. All appends of a level hit
+// one counter, so the sinks keep atomics on it rare:
+//   WarpSink  the 32 lanes of a warp append a batch together: one warp scan of
+//             the per-lane counts, then either one exact reservation per batch
+//             (chunk == 0) or slots from a warp-private run of `chunk` slots
+//             reserved ahead (unused slots are padded with -1 when the warp
+//             finishes, and parents skip -1);
+//   CtaSink   diverged lanes (a parent's serial loop) append into a shared-memory
+//             buffer of the CTA, flushed with one atomic per tile.
+struct WarpSink {
+  int* next;
+  int* count;
+  int chunk;
+  int base;
+  int left;
+  template <int K>
+  __device__ __forceinline__ void push(const bool (&pf)[K], const int (&v)[K]) {
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < K; k++) c += pf[k] ? 1 : 0;
+    const int lane = threadIdx.x & 31;
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += x;
+    }
+    const int total = __shfl_sync(kFull, inc, 31);
+    if (total == 0) return;
+    int r = inc - c;   // rank of this lane's first append within the warp's batch
+    if (chunk == 0) {
+      int b0 = 0;
+      if (lane == 31) b0 = atomicAdd(count, total);
+      b0 = __shfl_sync(kFull, b0, 31);
+#pragma unroll
+      for (int k = 0; k < K; k++)
+        if (pf[k]) next[b0 + r++] = v[k];
+      return;
+    }
+    const int need = total - left;   // appends beyond the current run
+    int nb = 0, nres = 0;
+    if (need > 0) {
+      nres = ceil_div(need, chunk) * chunk;
+      if (lane == 0) nb = atomicAdd(count, nres);
+      nb = __shfl_sync(kFull, nb, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      if (pf[k]) {
+        next[r < left ? base + r : nb + (r - left)] = v[k];
+        r++;
+      }
+    }
+    if (need > 0) {
+      base = nb + need;
+      left = nres - need;
+    } else {
+      base += total;
+      left -= total;
+    }
+  }
+  // pad the unused reserved slots (the next level skips ids < 0)
+  __device__ __forceinline__ void flush() {
+    for (int i = threadIdx.x & 31; i < left; i += 32) next[base + i] = -1;
+    left = 0;
+  }
+};
+
+constexpr int kStageSlots = 1024;   // shared-memory staging slots per parent CTA
+
+struct CtaSink {
+  int* next;
+  int* count;
+  int* q;    // shared staging buffer [kStageSlots]
+  int* qn;   // shared fill counter (may exceed kStageSlots: the excess went to global memory)
+  template <int K>
+  __device__ __forceinline__ void push(const bool (&pf)[K], const int (&v)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      if (!pf[k]) continue;
+      const int pos = atomicAdd(qn, 1);
+      if (pos < kStageSlots) {
+        q[pos] = v[k];
+      } else {
+        next[atomicAdd(count, 1)] = v[k];
+      }
+    }
+  }
+};
 
 // ------------------------------------------------------------------- bodies
+//
+// A body gives the child count of a parent (count), what every child of a
+// parent shares (parent), the loads of one child item (fetch) and the effect
+// of a batch of K items of one thread (apply_batch), which reports the
+// vertices to append to the next frontier. A batch issues all its loads, then
+// all its atomics, before it uses any of their results, so a thread keeps K
+// memory operations in flight.
 
 // BFS (Section VII): child item = out-edge u->v; claims v for level L+1.
 struct BfsBody {
   static constexpr bool kOffsets = false;
+  static constexpr bool kPushes = true;
   struct P {
     int base;
   };
@@ -306,17 +404,29 @@ struct BfsBody {
   }
   __device__ static P parent(const BodyArgs&, int, int base, int) { return P{base}; }
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) { return F{__ldg(&b.col[p.base + i])}; }
-  template <bool kFullWarp>
-  __device__ static void apply(const BodyArgs& b, const P&, int, const F& f, bool valid) {
-    bool claimed = false;
-    if (valid && b.level[f.v] == -1) claimed = atomicCAS(&b.level[f.v], -1, b.L + 1) == -1;
-    push_frontier<kFullWarp>(claimed, f.v, b.next, b.next_count);
+  template <int K>
+  __device__ static void apply_batch(const BodyArgs& b, const P&, const int (&)[K], const F (&f)[K],
+                                     const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
+    int cur[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      v[k] = f[k].v;
+      cur[k] = valid[k] ? __ldcg(&b.level[v[k]]) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      push[k] = valid[k] && cur[k] == -1;
+      if (push[k]) cur[k] = atomicCAS(&b.level[v[k]], -1, b.L + 1);
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) push[k] = push[k] && cur[k] == -1;
   }
 };
 
 // SSSP (Section VII): child item = relaxation of out-edge u->v with weight w.
 struct SsspBody {
   static constexpr bool kOffsets = false;
+  static constexpr bool kPushes = true;
   struct P {
     int base;
     unsigned du;
@@ -335,24 +445,35 @@ struct SsspBody {
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) {
     return F{__ldg(&b.col[p.base + i]), __ldg(&b.w[p.base + i])};
   }
-  template <bool kFullWarp>
-  __device__ static void apply(const BodyArgs& b, const P& p, int, const F& f, bool valid) {
-    bool push = false;
-    if (valid && p.du != 0xffffffffu) {
-      unsigned long long s = (unsigned long long)p.du + f.w;
-      unsigned nd = s >= 0xffffffffull ? 0xfffffffeu : (unsigned)s;
-      if (nd < b.dist[f.v]) {
-        unsigned old = atomicMin(&b.dist[f.v], nd);
-        if (nd < old) push = atomicExch(&b.stamp[f.v], b.L + 1) != b.L + 1;
-      }
+  template <int K>
+  __device__ static void apply_batch(const BodyArgs& b, const P& p, const int (&)[K], const F (&f)[K],
+                                     const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
+    const bool live = p.du != 0xffffffffu;
+    unsigned nd[K], cur[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      v[k] = f[k].v;
+      const unsigned long long s = (unsigned long long)p.du + f[k].w;
+      nd[k] = s >= 0xffffffffull ? 0xfffffffeu : (unsigned)s;
+      cur[k] = (valid[k] && live) ? __ldcg(&b.dist[v[k]]) : 0u;
     }
-    push_frontier<kFullWarp>(push, f.v, b.next, b.next_count);
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      push[k] = valid[k] && live && nd[k] < cur[k];
+      if (push[k]) cur[k] = atomicMin(&b.dist[v[k]], nd[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      push[k] = push[k] && nd[k] < cur[k];
+      if (push[k]) push[k] = atomicExch(&b.stamp[v[k]], b.L + 1) != b.L + 1;
+    }
   }
 };
 
 // BT (Section VII): parent = quadratic curve; child item j = point j.
 struct BezierBody {
   static constexpr bool kOffsets = true;
+  static constexpr bool kPushes = false;
   struct P {
     float x0, y0, x1, y1, x2, y2;
     int base;
@@ -385,44 +506,72 @@ struct BezierBody {
              (float)(N - 1)};
   }
   __device__ static F fetch(const BodyArgs&, const P&, int) { return F{}; }
-  template <bool kFullWarp>
-  __device__ static void apply(const BodyArgs& b, const P& p, int i, const F&, bool valid) {
-    if (!valid) return;
-    const float t = (float)i / p.denom;
-    const float u = 1.0f - t;
-    const float b0 = u * u, b1 = 2.0f * u * t, b2 = t * t;
-    b.points[p.base + i] = make_float2(b0 * p.x0 + b1 * p.x1 + b2 * p.x2, b0 * p.y0 + b1 * p.y1 + b2 * p.y2);
+  template <int K>
+  __device__ static void apply_batch(const BodyArgs& b, const P& p, const int (&idx)[K], const F (&)[K],
+                                     const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      push[k] = false;
+      v[k] = 0;
+      if (!valid[k]) continue;
+      const float t = (float)idx[k] / p.denom;
+      const float u = 1.0f - t;
+      const float b0 = u * u, b1 = 2.0f * u * t, b2 = t * t;
+      b.points[p.base + idx[k]] =
+          make_float2(b0 * p.x0 + b1 * p.x1 + b2 * p.x2, b0 * p.y0 + b1 * p.y1 + b2 * p.y2);
+    }
   }
 };
 
 // --------------------------------------------------------------- child side
 
 // One coarsened child block: CF consecutive original blocks of one parent
-// (Section IV-B; contiguous original blocks). Loads of all CF items are issued
-// before any of them is applied.
+// (Section IV-B; contiguous original blocks), in batches of up to 8 original
+// blocks whose items are all loaded before any is applied.
 template <class Body, int CF>
-__device__ __forceinline__ void run_coarsened(const BodyArgs& b, const typename Body::P& p, int N, int cb) {
-  const int B = blockDim.x, tid = threadIdx.x;
-  typename Body::F f[CF];
-  bool v[CF];
+__device__ __forceinline__ void run_coarsened(const BodyArgs& b, const typename Body::P& p, int N, int cb, int B,
+                                              int tid, WarpSink& sink) {
+  constexpr int KB = CF < 8 ? CF : 8;
 #pragma unroll
-  for (int k = 0; k < CF; k++) {
-    const int i = (cb * CF + k) * B + tid;
-    v[k] = i < N;
-    if (v[k]) f[k] = Body::fetch(b, p, i);
-  }
+  for (int k0 = 0; k0 < CF; k0 += KB) {
+    if ((cb * CF + k0) * B >= N) break;   // uniform across the block
+    typename Body::F f[KB];
+    bool v[KB];
+    int idx[KB];
 #pragma unroll
-  for (int k = 0; k < CF; k++) {
-    const int i0 = (cb * CF + k) * B;
-    if (i0 < N) Body::template apply<true>(b, p, i0 + tid, f[k], v[k]);
+    for (int k = 0; k < KB; k++) {
+      idx[k] = (cb * CF + k0 + k) * B + tid;
+      v[k] = idx[k] < N;
+      f[k] = v[k] ? Body::fetch(b, p, idx[k]) : typename Body::F{};
+    }
+    bool pf[KB];
+    int pv[KB];
+    Body::template apply_batch<KB>(b, p, idx, f, v, pf, pv);
+    if constexpr (Body::kPushes) sink.template push<KB>(pf, pv);
   }
 }
 
-// Serial version of a parent's children (thresholding's fallback, the NODP form).
+// Serial version of a parent's children (thresholding's fallback, the NODP
+// form): the parent thread walks its children in order, four at a time.
 template <class Body>
-__device__ __forceinline__ void run_serial(const BodyArgs& b, int pid, int base, int N) {
+__device__ __forceinline__ void run_serial(const BodyArgs& b, int pid, int base, int N, CtaSink& sink) {
+  constexpr int KS = 4;
   const typename Body::P p = Body::parent(b, pid, base, N);
-  for (int i = 0; i < N; i++) Body::template apply<false>(b, p, i, Body::fetch(b, p, i), true);
+  for (int i0 = 0; i0 < N; i0 += KS) {
+    typename Body::F f[KS];
+    bool v[KS];
+    int idx[KS];
+#pragma unroll
+    for (int k = 0; k < KS; k++) {
+      idx[k] = i0 + k;
+      v[k] = idx[k] < N;
+      f[k] = v[k] ? Body::fetch(b, p, idx[k]) : typename Body::F{};
+    }
+    bool pf[KS];
+    int pv[KS];
+    Body::template apply_batch<KS>(b, p, idx, f, v, pf, pv);
+    if constexpr (Body::kPushes) sink.template push<KS>(pf, pv);
+  }
 }
 
 __device__ __forceinline__ void add_stat(LevelState* st, int k, unsigned long long v) {
@@ -453,12 +602,16 @@ __device__ __forceinline__ void advance_level(LevelState* st) {
 template <class Body, int CF>
 __global__ void __launch_bounds__(1024) child_direct(BodyArgs b, int pid, int base, int N) {
   const typename Body::P p = Body::parent(b, pid, base, N);
-  run_coarsened<Body, CF>(b, p, N, blockIdx.x);
+  WarpSink sink{b.next, b.next_count, 0, 0, 0};
+  run_coarsened<Body, CF>(b, p, N, blockIdx.x, blockDim.x, threadIdx.x, sink);
 }
 
-// Aggregated child grid: disaggregation + coarsened body. Persistent over the
-// aggregated blocks when launched with fewer CTAs than blocks (grid-host form,
-// whose size is read from device memory).
+// Aggregated child grid: disaggregation + coarsened body. A CTA hosts
+// blockDim.x / cb child blocks of cb threads that run independently (no CTA
+// barrier on this path). When launched with fewer child blocks than
+// aggregated blocks (the grid-host form, whose size is read from device
+// memory) each child block takes a contiguous range of aggregated blocks, so
+// after the first search the parent index only moves forward.
 template <class Body, int CF>
 __global__ void __launch_bounds__(1024) child_agg(BodyArgs b, AggSeg s) {
   int nrec = s.nrec, total = s.total;
@@ -477,23 +630,32 @@ __global__ void __launch_bounds__(1024) child_agg(BodyArgs b, AggSeg s) {
     b.next = (L & 1) ? s.fr0 : s.fr1;
     b.next_count = &st->count[(L + 1) % 3];
   }
-  int lo = 0;
-  unsigned long long blocks = 0;
-  for (int B0 = blockIdx.x; B0 < total; B0 += gridDim.x) {
-    const int j = disaggregate(s.boff, lo, nrec, B0);
-    const int4 r = __ldcg(&s.rec[j]);
-    const int off = __ldcg(&s.boff[j]);
-    const typename Body::P p = Body::parent(b, r.x, r.y, r.z);
-    run_coarsened<Body, CF>(b, p, r.z, B0 - off);
-    lo = j;
-    blocks++;
+  const int cb = s.cb, per_cta = (int)blockDim.x / cb;
+  const int sub = (int)blockIdx.x * per_cta + (int)threadIdx.x / cb, stid = (int)threadIdx.x % cb;
+  const int chunk = ceil_div(total, (int)gridDim.x * per_cta);
+  const int first = sub * chunk;
+  const int last = min(total, first + chunk);
+  int j = -1, next_off = 0, off = 0, N = 0;
+  typename Body::P p{};
+  WarpSink sink{b.next, b.next_count, s.qchunk, 0, 0};
+  for (int B0 = first; B0 < last; B0++) {
+    if (j < 0 || B0 >= next_off) {
+      j = j < 0 ? warp_search(s.boff, 0, nrec, B0) : warp_search_near(s.boff, j + 1, nrec, B0);
+      const int4 r = __ldcg(&s.rec[j]);
+      off = __ldcg(&s.boff[j]);
+      next_off = j + 1 < nrec ? __ldcg(&s.boff[j + 1]) : 0x7fffffff;
+      N = r.z;
+      p = Body::parent(b, r.x, r.y, r.z);
+    }
+    run_coarsened<Body, CF>(b, p, N, B0 - off, cb, stid, sink);
   }
+  sink.flush();
   if (s.mode != 0) {
     // persistent (grid-host) form: count its blocks here; device-launched
     // grids are counted by the launching parent
     __syncthreads();
+    if (stid == 0) add_stat(st, S_CBLOCKS, (unsigned long long)max(last - first, 0));
     if (threadIdx.x == 0) {
-      add_stat(st, S_CBLOCKS, blocks);
       if (s.advance) {
         __threadfence();
         if (atomicAdd(&st->child_done, 1) == (int)gridDim.x - 1) {
@@ -509,13 +671,13 @@ __global__ void __launch_bounds__(1024) child_agg(BodyArgs b, AggSeg s) {
 
 template <class Body, int CF>
 __device__ __forceinline__ void launch_direct(const BodyArgs& b, int pid, int base, int N, int child_block,
-                                              unsigned* s_stat) {
+                                              unsigned* s_stat, CtaSink& sink) {
   const int cg = ceil_div(ceil_div(N, child_block), CF);
   child_direct<Body, CF><<<cg, child_block, 0, cudaStreamFireAndForget>>>(b, pid, base, N);
   if (cudaGetLastError() != cudaSuccess) {
     atomicOr(&b.st->error, kErrLaunch);
     atomicAdd(&s_stat[S_LFAIL], 1u);
-    run_serial<Body>(b, pid, base, N);
+    run_serial<Body>(b, pid, base, N, sink);
   } else {
     atomicAdd(&s_stat[S_DEVLAUNCH], 1u);
     atomicAdd(&s_stat[S_CBLOCKS], (unsigned)cg);
@@ -524,8 +686,8 @@ __device__ __forceinline__ void launch_direct(const BodyArgs& b, int pid, int ba
 
 template <class Body, int CF>
 __device__ __forceinline__ void launch_aggregated(const BodyArgs& b, const int4* rec, const int* boff, int nrec,
-                                                  int total, int child_block, unsigned* s_stat) {
-  AggSeg s{rec, boff, nullptr, nullptr, nrec, total, 0, 0, 0, 0};
+                                                  int total, int child_block, unsigned* s_stat, CtaSink& sink) {
+  AggSeg s{rec, boff, nullptr, nullptr, nrec, total, 0, 0, 0, child_block, 0, 0};
   child_agg<Body, CF><<<total, child_block, 0, cudaStreamFireAndForget>>>(b, s);
   if (cudaGetLastError() != cudaSuccess) {
     // run the aggregated grid's work in this thread: parent by parent, serially
@@ -533,7 +695,7 @@ __device__ __forceinline__ void launch_aggregated(const BodyArgs& b, const int4*
     atomicAdd(&s_stat[S_LFAIL], 1u);
     for (int j = 0; j < nrec; j++) {
       const int4 r = __ldcg(&rec[j]);
-      run_serial<Body>(b, r.x, r.y, r.z);
+      run_serial<Body>(b, r.x, r.y, r.z, sink);
     }
   } else {
     atomicAdd(&s_stat[S_DEVLAUNCH], 1u);
@@ -542,14 +704,24 @@ __device__ __forceinline__ void launch_aggregated(const BodyArgs& b, const int4*
   }
 }
 
+__device__ __forceinline__ void warp_stat(unsigned* s_stat, int k, unsigned v) {
+  const unsigned t = __reduce_add_sync(kFull, v);
+  if ((threadIdx.x & 31) == 0 && t) atomicAdd(&s_stat[k], t);
+}
+
 // The parent kernel of one level. GRAN selects the form; CF is the coarsening
-// factor of the child kernel it launches (device-launch forms only).
+// factor of the child kernel it launches (device-launch forms only). Per tile:
+// child counts, output offsets (Bezier), the launch decision, the aggregation
+// scan, records and launch; the serial children of the parents below the
+// threshold come last, so no scan ever waits behind a serial loop.
 template <class Body, int GRAN, int CF>
 __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
   __shared__ int s_tile;
   __shared__ uint2 s_scan[33];
   __shared__ V3 s_v3;
   __shared__ unsigned s_stat[S_N];
+  __shared__ int s_q[kStageSlots];
+  __shared__ int s_qn, s_qflush, s_qbase;
   const int tid = threadIdx.x, PB = blockDim.x, lane = tid & 31, warp = tid >> 5;
   LevelState* st = a.st;
   const bool fixed = a.count_fixed >= 0;
@@ -564,24 +736,30 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
   b.next = fixed ? a.next_ovr : ((L & 1) ? a.fr0 : a.fr1);
   b.next_count = fixed ? a.next_count_ovr : &st->count[(L + 1) % 3];
   const int ntiles = ceil_div(count, PB);
+  // CTAs beyond the number of tiles have nothing to take: leave at once
+  // (the level's last CTA is then the last of the first min(grid, tiles))
+  const int active = min((int)gridDim.x, ntiles);
+  if ((int)blockIdx.x >= active) return;
   const int T = a.threshold < 1 ? 1 : a.threshold;
   const int CB = a.child_block;
   if (tid < S_N) s_stat[tid] = 0;
+  CtaSink sink{b.next, b.next_count, s_q, &s_qn};
   __syncthreads();
 
   for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&st->ticket, 1);
+    if (tid == 0) {
+      s_tile = atomicAdd(&st->ticket, 1);
+      s_qn = 0;
+    }
     __syncthreads();
     const int tile = s_tile;
     __syncthreads();
     if (tile >= ntiles) break;
     const int i = tile * PB + tid;
-    const bool valid = i < count;
     int pid = 0, base = 0, N = 0;
-    if (valid) {
-      pid = ids ? __ldcg(&ids[i]) : i;
-      Body::count(a, pid, base, N);
-    }
+    if (i < count) pid = ids ? __ldcg(&ids[i]) : i;
+    const bool valid = i < count && pid >= 0;   // frontier slots padded with -1 hold no parent
+    if (valid) Body::count(a, pid, base, N);
     if constexpr (Body::kOffsets) {
       // output offsets: exclusive scan of N over all parents, in parent order
       unsigned e0, e1, t0, t1;
@@ -601,33 +779,22 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
         N = 0;
       }
     }
-    if (valid) {
-      atomicAdd(&s_stat[S_PARENTS], 1u);
-      atomicAdd(&s_stat[S_ITEMS], (unsigned)N);
-    }
-    if constexpr (GRAN == G_NODP) {
-      if (valid && N > 0) {
-        atomicAdd(&s_stat[S_SERIAL], 1u);
-        run_serial<Body>(b, pid, base, N);
-      }
-    } else {
-      const bool launch = valid && N >= T;
-      if (valid && !launch && N > 0) {
-        atomicAdd(&s_stat[S_SERIAL], 1u);
-        run_serial<Body>(b, pid, base, N);
-      }
-      if (launch) {
-        atomicAdd(&s_stat[S_LAUNCHP], 1u);
-        atomicAdd(&s_stat[S_CITEMS], (unsigned)N);
-      }
+    const bool launch = GRAN != G_NODP && valid && N >= T;
+    const bool serial = valid && !launch && N > 0;
+    warp_stat(s_stat, S_PARENTS, valid ? 1u : 0u);
+    warp_stat(s_stat, S_ITEMS, (unsigned)N);
+    warp_stat(s_stat, S_SERIAL, serial ? 1u : 0u);
+    if constexpr (GRAN != G_NODP) {
+      warp_stat(s_stat, S_LAUNCHP, launch ? 1u : 0u);
+      warp_stat(s_stat, S_CITEMS, launch ? (unsigned)N : 0u);
       const unsigned cg = launch ? (unsigned)ceil_div(ceil_div(N, CB), a.cfactor) : 0u;
       if constexpr (GRAN == G_NONE) {
-        if (launch) launch_direct<Body, CF>(b, pid, base, N, CB, s_stat);
+        if (launch) launch_direct<Body, CF>(b, pid, base, N, CB, s_stat, sink);
       } else if constexpr (GRAN == G_WARP) {
         const unsigned m = __ballot_sync(kFull, launch);
         const int np = __popc(m);
         if (np > 0 && np < a.agg_threshold) {
-          if (launch) launch_direct<Body, CF>(b, pid, base, N, CB, s_stat);
+          if (launch) launch_direct<Body, CF>(b, pid, base, N, CB, s_stat, sink);
         } else if (np > 0) {
           unsigned inc = cg;
 #pragma unroll
@@ -645,13 +812,13 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
           __threadfence();
           __syncwarp();
           if (lane == 31 - __clz(m))
-            launch_aggregated<Body, CF>(b, a.rec + seg, a.boff + seg, np, (int)total, CB, s_stat);
+            launch_aggregated<Body, CF>(b, a.rec + seg, a.boff + seg, np, (int)total, CB, s_stat, sink);
         }
       } else if constexpr (GRAN == G_BLOCK) {
         unsigned ea, eb, ta, tb;
         block_scan2(launch ? 1u : 0u, cg, ea, eb, ta, tb, s_scan);
         if ((int)ta < a.agg_threshold) {
-          if (launch) launch_direct<Body, CF>(b, pid, base, N, CB, s_stat);
+          if (launch) launch_direct<Body, CF>(b, pid, base, N, CB, s_stat, sink);
         } else {
           const int seg = tile * PB;
           if (launch) {
@@ -660,7 +827,7 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
           }
           __threadfence();
           __syncthreads();
-          if (tid == 0 && ta > 0) launch_aggregated<Body, CF>(b, a.rec + seg, a.boff + seg, (int)ta, (int)tb, CB, s_stat);
+          if (tid == 0 && ta > 0) launch_aggregated<Body, CF>(b, a.rec + seg, a.boff + seg, (int)ta, (int)tb, CB, s_stat, sink);
         }
       } else {
         // multi-block / grid granularity: the scope is a group of G tiles
@@ -690,7 +857,6 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
             st->agg_records = (int)(x.a + ta);
             st->agg_blocks = (int)(x.b + tb);
           }
-          __syncthreads();
         } else {
           if (a.scan == 0 && tile == first + gsize - 1 && tid == 0) a.grp_total[g] = make_uint2(x.a + ta, x.b + tb);
           __threadfence();
@@ -710,13 +876,25 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
                 nblk = (unsigned)(t & ((1ull << 40) - 1));
               }
               a.grp_ctr[g] = 0;
-              if (nrec > 0) launch_aggregated<Body, CF>(b, a.rec + seg, a.boff + seg, (int)nrec, (int)nblk, CB, s_stat);
+              if (nrec > 0) launch_aggregated<Body, CF>(b, a.rec + seg, a.boff + seg, (int)nrec, (int)nblk, CB, s_stat, sink);
             }
           }
         }
       }
     }
+    // serialised children last (thresholding's fallback; every child in NODP)
+    if (serial) run_serial<Body>(b, pid, base, N, sink);
     __syncthreads();
+    if constexpr (Body::kPushes) {
+      // flush the tile's staged appends: one atomic on the level counter
+      if (tid == 0) {
+        const int n = min(s_qn, kStageSlots);
+        s_qflush = n;
+        s_qbase = n > 0 ? atomicAdd(b.next_count, n) : 0;
+      }
+      __syncthreads();
+      for (int k = tid; k < s_qflush; k += PB) b.next[s_qbase + k] = s_q[k];
+    }
   }
 
   __syncthreads();
@@ -725,7 +903,7 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      if (atomicAdd(&st->parent_done, 1) == (int)gridDim.x - 1) {
+      if (atomicAdd(&st->parent_done, 1) == active - 1) {
         __threadfence();
         advance_level(st);
       }

@@ -155,12 +155,15 @@ extern "C" np_status np_bezier_noalloc(const float* ctrl, int32_t ncurves, int32
     seg.rec = a.rec;
     seg.boff = a.boff;
     seg.mode = a.scan == NP_SCAN_LOOKBACK ? 1 : 2;
+    seg.cb = cb;
+    const int cthreads = cb < 256 ? 256 : cb;
     BodyArgs b = a.b;
     int cocc = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cocc, K.child_agg[cfi], cb, 0) != cudaSuccess || cocc < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cocc, K.child_agg[cfi], cthreads, 0) != cudaSuccess ||
+        cocc < 1)
       cocc = 1;
     void* cargs[] = {&b, &seg};
-    if (cudaLaunchKernel(K.child_agg[cfi], dim3(cocc * d.sms), dim3(cb), cargs, 0, s) != cudaSuccess)
+    if (cudaLaunchKernel(K.child_agg[cfi], dim3(cocc * d.sms), dim3(cthreads), cargs, 0, s) != cudaSuccess)
       return NP_ERR_CUDA;
   }
   return NP_OK;

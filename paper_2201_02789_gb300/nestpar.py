@@ -75,13 +75,25 @@ class np_stats(ctypes.Structure):
         return {f: int(getattr(self, f)) for f, _ in self._fields_ if f != "reserved"}
 
 
+NP_PROFILE_LEVELS = 64
+
+
 class np_profile(ctypes.Structure):
     _fields_ = [("parent_ms", ctypes.c_double), ("child_ms", ctypes.c_double), ("other_ms", ctypes.c_double),
                 ("parent_launches", ctypes.c_int64), ("child_launches", ctypes.c_int64),
-                ("other_launches", ctypes.c_int64)]
+                ("other_launches", ctypes.c_int64), ("longest_level_ms", ctypes.c_double),
+                ("levels", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("level_parents", ctypes.c_int32 * NP_PROFILE_LEVELS),
+                ("level_parent_ms", ctypes.c_double * NP_PROFILE_LEVELS),
+                ("level_child_ms", ctypes.c_double * NP_PROFILE_LEVELS)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_[:8]}
+        n = min(self.levels, NP_PROFILE_LEVELS)
+        d["level_parents"] = list(self.level_parents[:n])
+        d["level_parent_ms"] = list(self.level_parent_ms[:n])
+        d["level_child_ms"] = list(self.level_child_ms[:n])
+        return d
 
 
 class np_parents(ctypes.Structure):

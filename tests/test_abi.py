@@ -58,6 +58,7 @@ int main(void) {
   printf("np_stats %zu %zu %zu\n", sizeof(np_stats), offsetof(np_stats, timeouts), offsetof(np_stats, error));
   printf("np_parents %zu %zu %zu\n", sizeof(np_parents), offsetof(np_parents, ids), offsetof(np_parents, count));
   printf("np_body %zu %zu %zu\n", sizeof(np_body), offsetof(np_body, level), offsetof(np_body, cap));
+  printf("np_profile %zu %zu %zu\n", sizeof(np_profile), offsetof(np_profile, levels), offsetof(np_profile, level_child_ms));
   return 0;
 }
 ''')
@@ -70,6 +71,7 @@ int main(void) {
         "np_stats": (npb.np_stats, "timeouts", "error"),
         "np_parents": (npb.np_parents, "ids", "count"),
         "np_body": (npb.np_body, "level", "cap"),
+        "np_profile": (npb.np_profile, "levels", "level_child_ms"),
     }
     for name, (cls, f1, f2) in py.items():
         assert rows[name] == [ctypes.sizeof(cls), getattr(cls, f1).offset, getattr(cls, f2).offset], name
@@ -79,7 +81,8 @@ def test_host_only_entry_points(lib):
     assert npb.np_version() == 10000
     assert npb.np_status_string(npb.NP_ERR_INVALID) == "invalid argument"
     cfg = npb.np_config_default()
-    assert (cfg.variant, cfg.threshold, cfg.cfactor, cfg.granularity) == (1, 128, 8, npb.NP_GRAN_GRID_HOST)
+    assert (cfg.variant, cfg.threshold, cfg.cfactor, cfg.granularity) == (1, 32, 8, npb.NP_GRAN_GRID_HOST)
+    assert cfg.child_block == 32
     assert npb.np_workspace_size(1 << 20, cfg) > (1 << 20) * 16
     with pytest.raises(npb.NestparError):
         npb.np_workspace_size(-1, cfg)
@@ -92,7 +95,7 @@ def test_named_forms():
     f = {k: npb.config(k) for k in ("nodp", "cdp", "t", "c", "tc", "a", "ta", "ca", "tca")}
     assert f["nodp"].variant == npb.NP_VARIANT_NODP
     assert (f["cdp"].threshold, f["cdp"].cfactor, f["cdp"].granularity) == (0, 1, npb.NP_GRAN_NONE)
-    assert f["tca"].granularity == npb.NP_GRAN_GRID_HOST and f["tca"].threshold == 128
+    assert f["tca"].granularity == npb.NP_GRAN_GRID_HOST and f["tca"].threshold == 32
     assert npb.config("tca", granularity="multiblock").granularity == npb.NP_GRAN_MULTIBLOCK
 
 
