@@ -42,16 +42,22 @@ def stale() -> bool:
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link if any source changed; returns the library path."""
-    if not force and not stale():
+def build(force: bool = False, verbose: bool = False, defines: tuple[str, ...] = (), out_dir: str | None = None) -> str:
+    """Compile and link if any source changed; returns the library path.
+
+    ``defines`` (``NAME=VALUE`` strings) and ``out_dir`` build a variant of the
+    library elsewhere, for tuning experiments; the default build uses neither."""
+    bdir = out_dir or BUILD
+    lib = os.path.join(bdir, "libnestpar.so")
+    if out_dir is None and not force and not stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
+    dflags = ["-D" + d for d in defines]
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *CFLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *CFLAGS, *dflags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -61,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     # export the C ABI only: the statically linked CUDA runtime stays private, so
     # it can never be interposed by another runtime loaded in the same process
     cmd = [cc, *ARCH, "-shared", "-rdc=true", "-Xcompiler", "-fPIC",
@@ -70,8 +76,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

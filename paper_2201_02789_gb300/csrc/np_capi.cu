@@ -28,8 +28,19 @@ namespace {
 
 constexpr int kVersion = 10000;  // 1.0.0
 constexpr size_t kAlign = 256;
-constexpr int kQueueChunk = 32;    // frontier slots a child warp reserves at a time (level mode)
-constexpr int kMaxWarpsPerSM = 64;
+
+
+__device__ __forceinline__ void reset_slots(LevelState* st) {
+  for (int k = 0; k < 4; k++) {
+    st->ticket[k] = 0;
+    st->agg_records[k] = 0;
+    st->agg_blocks[k] = 0;
+    st->agg_acc[k] = 0ull;
+  }
+  for (int k = 0; k < S_N; k++) st->s[k] = 0ull;
+  st->body_iters = 0;
+  st->solve_id += 1;
+}
 
 __global__ void init_solve_kernel(LevelState* st, int kind, int n, int src, int* level, unsigned* dist,
                                   int* stamp, int* fr0, int max_levels) {
@@ -43,41 +54,26 @@ __global__ void init_solve_kernel(LevelState* st, int kind, int n, int src, int*
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     fr0[0] = src;
-    st->level = 0;
-    st->max_levels = max_levels;
-    st->epoch += 1;
-    st->ticket = 0;
-    st->parent_done = 0;
-    st->child_done = 0;
+    st->base = 0;
     st->count[0] = 1;
     st->count[1] = 0;
     st->count[2] = 0;
-    st->agg_records = 0;
-    st->agg_blocks = 0;
-    st->agg_acc = 0ull;
-    st->body_iters = 0;
-    for (int k = 0; k < S_N; k++) st->s[k] = 0ull;
+    st->max_levels = max_levels;
+    reset_slots(st);
   }
 }
 
-__global__ void init_fixed_kernel(LevelState* st) {
-  st->epoch += 1;
-  st->body_iters = 0;
-  st->ticket = 0;
-  st->parent_done = 0;
-  st->child_done = 0;
-  st->agg_records = 0;
-  st->agg_blocks = 0;
-  st->agg_acc = 0ull;
-  for (int k = 0; k < S_N; k++) st->s[k] = 0ull;
-}
+__global__ void init_fixed_kernel(LevelState* st) { reset_slots(st); }
 
-__global__ void advance_kernel(LevelState* st) { advance_level(st); }
+// Between graph bodies or chunks: the next body position 0 is level base + K.
+__global__ void advance_base_kernel(LevelState* st, int K) { st->base += K; }
 
-// Ends the while loop when the frontier is empty. The iteration cap turns a
-// level that failed to advance into an error instead of an endless loop.
-__global__ void set_cond_kernel(LevelState* st, cudaGraphConditionalHandle h) {
-  const int L = st->level;
+// End of a conditional-while body of K levels: move base on and continue while
+// the next level has parents. The iteration cap turns a level loop that failed
+// to terminate into an error instead of an endless loop.
+__global__ void set_cond_kernel(LevelState* st, cudaGraphConditionalHandle h, int K) {
+  const int L = st->base + K;
+  st->base = L;
   const int c = st->count[L % 3];
   const int it = ++st->body_iters;
   bool more = c > 0 && L < st->max_levels;
@@ -110,13 +106,13 @@ struct Layout {
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Frontier buffers hold up to `parents` appends plus the padding of the
-// warp-private runs of the persistent child grid (at most kQueueChunk per warp).
+// Frontier buffers hold up to `parents` appends (exact appends: no padding).
 Layout layout_for(int64_t parents, int sms) {
+  (void)sms;
   Layout L{};
   L.P2 = ((parents + 1023) / 1024) * 1024 + 1024;
   L.T = L.P2 / 32 + 64;
-  const int64_t fr = L.P2 + (int64_t)(sms > 0 ? sms : 256) * kMaxWarpsPerSM * kQueueChunk;
+  const int64_t fr = L.P2;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t r = o;
@@ -320,9 +316,10 @@ Grids grids_for(np_ctx* c, const Plan& p, const np_config& cfg, int64_t max_pare
   return g;
 }
 
-// Enqueues the grids of one level (level mode) or of one fixed pass.
-np_status enqueue_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool level_mode, cudaStream_t s) {
-  a.advance = (level_mode && p.mode == M_NODP) ? 1 : 0;
+// Enqueues the grids of one level (level mode, at body position k) or of one
+// fixed pass.
+np_status enqueue_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool level_mode, int k, cudaStream_t s) {
+  a.k = level_mode ? k : 0;
   void* pargs[] = {&a};
   NP_CK(cudaLaunchKernel(p.parent, dim3(g.pgrid), dim3(g.pblock), pargs, 0, s));
   if (p.mode == M_GRID_HOST) {
@@ -330,12 +327,11 @@ np_status enqueue_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool le
     seg.rec = a.rec;
     seg.boff = a.boff;
     seg.mode = a.scan == 0 ? 1 : 2;
-    seg.advance = level_mode ? 1 : 0;
+    seg.k = a.k;
     seg.level_mode = level_mode ? 1 : 0;
     seg.fr0 = a.fr0;
     seg.fr1 = a.fr1;
     seg.cb = g.cblock;
-    seg.qchunk = level_mode ? kQueueChunk : 0;
     BodyArgs b = a.b;
     if (!level_mode) {
       b.L = a.L_fixed;
@@ -344,33 +340,36 @@ np_status enqueue_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool le
     }
     void* cargs[] = {&b, &seg};
     NP_CK(cudaLaunchKernel(p.child, dim3(g.cgrid), dim3(g.cthreads), cargs, 0, s));
-  } else if (p.mode == M_DEVICE_LAUNCH && level_mode) {
-    advance_kernel<<<1, 1, 0, s>>>(c->st);
-    NP_CK(cudaGetLastError());
   }
+  return NP_OK;
+}
+
+np_status enqueue_advance(np_ctx* c, int K, cudaStream_t s) {
+  advance_base_kernel<<<1, 1, 0, s>>>(c->st, K);
+  NP_CK(cudaGetLastError());
   return NP_OK;
 }
 
 // Profile mode: the grids of one level (or pass) launched one by one between
 // CUDA events, then waited for; times go to the context's breakdown.
 np_status profiled_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool level_mode, cudaStream_t s) {
-  a.advance = (level_mode && p.mode == M_NODP) ? 1 : 0;
+  a.k = 0;
   void* pargs[] = {&a};
   NP_CK(cudaEventRecord(c->ev[0], s));
   NP_CK(cudaLaunchKernel(p.parent, dim3(g.pgrid), dim3(g.pblock), pargs, 0, s));
   NP_CK(cudaEventRecord(c->ev[1], s));
   bool child = false, other = false;
+  cudaEvent_t child_end = c->ev[2];
   if (p.mode == M_GRID_HOST) {
     AggSeg seg{};
     seg.rec = a.rec;
     seg.boff = a.boff;
     seg.mode = a.scan == 0 ? 1 : 2;
-    seg.advance = level_mode ? 1 : 0;
+    seg.k = 0;
     seg.level_mode = level_mode ? 1 : 0;
     seg.fr0 = a.fr0;
     seg.fr1 = a.fr1;
     seg.cb = g.cblock;
-    seg.qchunk = level_mode ? kQueueChunk : 0;
     BodyArgs b = a.b;
     if (!level_mode) {
       b.L = a.L_fixed;
@@ -380,23 +379,27 @@ np_status profiled_pass(np_ctx* c, const Plan& p, Args a, const Grids& g, bool l
     void* cargs[] = {&b, &seg};
     NP_CK(cudaLaunchKernel(p.child, dim3(g.cgrid), dim3(g.cthreads), cargs, 0, s));
     child = true;
-  } else if (p.mode == M_DEVICE_LAUNCH && level_mode) {
-    advance_kernel<<<1, 1, 0, s>>>(c->st);
+  }
+  NP_CK(cudaEventRecord(child_end, s));
+  if (level_mode) {
+    advance_base_kernel<<<1, 1, 0, s>>>(c->st, 1);
     NP_CK(cudaGetLastError());
     other = true;
   }
-  NP_CK(cudaEventRecord(c->ev[2], s));
-  NP_CK(cudaEventSynchronize(c->ev[2]));
-  float t01 = 0.f, t12 = 0.f;
+  NP_CK(cudaEventRecord(c->ev[3], s));
+  NP_CK(cudaEventSynchronize(c->ev[3]));
+  float t01 = 0.f, t12 = 0.f, t23 = 0.f;
   NP_CK(cudaEventElapsedTime(&t01, c->ev[0], c->ev[1]));
   NP_CK(cudaEventElapsedTime(&t12, c->ev[1], c->ev[2]));
+  NP_CK(cudaEventElapsedTime(&t23, c->ev[2], c->ev[3]));
   c->prof.parent_ms += t01;
   c->prof.parent_launches += 1;
   if (child) {
     c->prof.child_ms += t12;
     c->prof.child_launches += 1;
-  } else if (other) {
-    c->prof.other_ms += t12;
+  }
+  if (other) {
+    c->prof.other_ms += t23;
     c->prof.other_launches += 1;
   }
   if (level_mode) {
@@ -446,7 +449,8 @@ np_status chunk_graph(np_ctx* c, const Plan& p, const Args& a, const Grids& g, i
   }
   NP_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   np_status st = NP_OK;
-  for (int k = 0; k < K && st == NP_OK; k++) st = enqueue_pass(c, p, a, g, true, c->cap_stream);
+  for (int k = 0; k < K && st == NP_OK; k++) st = enqueue_pass(c, p, a, g, true, k, c->cap_stream);
+  if (st == NP_OK) st = enqueue_advance(c, K, c->cap_stream);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
   if (st != NP_OK) {
@@ -491,8 +495,8 @@ np_status while_graph(np_ctx* c, const Plan& p, const Args& a, const Grids& g, i
     return from_cuda(e);
   }
   np_status st = NP_OK;
-  for (int k = 0; k < K && st == NP_OK; k++) st = enqueue_pass(c, p, a, g, true, c->cap_stream);
-  set_cond_kernel<<<1, 1, 0, c->cap_stream>>>(c->st, h);
+  for (int k = 0; k < K && st == NP_OK; k++) st = enqueue_pass(c, p, a, g, true, k, c->cap_stream);
+  set_cond_kernel<<<1, 1, 0, c->cap_stream>>>(c->st, h, K);
   cudaError_t le = cudaGetLastError();
   e = cudaStreamEndCapture(c->cap_stream, &body);
   if (st != NP_OK || le != cudaSuccess || e != cudaSuccess) {
@@ -504,11 +508,10 @@ np_status while_graph(np_ctx* c, const Plan& p, const Args& a, const Grids& g, i
 }
 
 np_status read_header(np_ctx* c, cudaStream_t s, int* level, int* count) {
-  NP_CK(cudaMemcpyAsync(c->pin, c->st, 12 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  NP_CK(cudaMemcpyAsync(c->pin, c->st, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));   // base, count[3]
   NP_CK(cudaStreamSynchronize(s));
-  const LevelState* h = reinterpret_cast<const LevelState*>(c->pin);
-  *level = h->level;
-  *count = h->count[h->level % 3];
+  *level = c->pin[0];
+  *count = c->pin[1 + c->pin[0] % 3];
   return NP_OK;
 }
 
@@ -580,7 +583,8 @@ np_status run_levels(np_ctx* c, const Plan& p, const Args& a, const np_config& c
     if (exec) {
       NP_CK(cudaGraphLaunch(exec, s));
     } else {
-      np_status st = enqueue_pass(c, p, a, g, true, s);
+      np_status st = enqueue_pass(c, p, a, g, true, 0, s);
+      if (st == NP_OK) st = enqueue_advance(c, 1, s);
       if (st != NP_OK) return st;
     }
     int level = 0, count = 0;
@@ -665,7 +669,7 @@ np_status fixed_pass(np_ctx* c, const Args& a0, const np_config& cfg, const Body
     NP_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     init_fixed_kernel<<<1, 1, 0, c->cap_stream>>>(c->st);
     cudaError_t le = cudaGetLastError();
-    np_status st = le == cudaSuccess ? enqueue_pass(c, p, a, g, false, c->cap_stream) : from_cuda(le);
+    np_status st = le == cudaSuccess ? enqueue_pass(c, p, a, g, false, 0, c->cap_stream) : from_cuda(le);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
     if (st != NP_OK) {

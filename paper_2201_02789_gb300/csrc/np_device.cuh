@@ -1,10 +1,13 @@
 // Device side of the nested-parallelism engine (sm_103a).
 //
-// One "level" runs the children of a set of parents. Parents are processed by
-// persistent CTAs that take tiles of `parent_block` parents from an atomic
-// ticket (tile order = parent order, and a CTA only ever waits on tiles that
-// running CTAs already own). For every parent the child count N is computed
-// (Section III-D: the number of child threads, not gDim * bDim), then:
+// One "level" runs the children of a set of parents. Parents are processed in
+// tiles taken from an atomic ticket, so tile order = parent order and a tile
+// only ever waits (in a look-back) on tiles that running threads already own:
+// warp-sized tiles for the forms without device launches (parent_warp), tiles
+// of `parent_block` parents per CTA for the device-launch forms, whose block
+// granularity needs CTA tiles (parent_kernel). For every parent the child
+// count N is computed (Section III-D: the number of child threads, not
+// gDim * bDim), then:
 //
 //   NODP        the parent loops over its N children (no launch code at all);
 //   N < T       the parent loops over its children (thresholding, Section III-A);
@@ -17,12 +20,37 @@
 // of a group of blocks or of the whole grid, or the paper's packed 64-bit
 // atomic), stores one record {parent, row start, N} per launching parent and
 // the scanned block offset, and one thread launches Sum(cg) blocks. Each
-// aggregated child block finds its parent by a k-ary search (k = block size)
-// over the offsets staged through __syncthreads_count, then runs CF original
-// blocks of that parent (disaggregation outside the coarsening loop, Section VI).
+// aggregated child block finds its parent by a 32-ary warp search over the
+// offsets, then runs CF original blocks of that parent (disaggregation outside
+// the coarsening loop, Section VI).
+//
+// Level bookkeeping is slot based so that no kernel has to finish a level:
+// level L = base + k, where base only changes between graph bodies and k is
+// the kernel's position in the body; per-level counters live in slot L % 4,
+// and the parent grid of level L clears the slot and frontier count that
+// level L + 2 will use.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+// Tuning knobs (compile time): items a child thread keeps in flight, items a
+// serialising parent thread keeps in flight, optional register caps.
+#ifndef NP_CHILD_BATCH
+#define NP_CHILD_BATCH 8
+#endif
+#ifndef NP_SERIAL_BATCH
+#define NP_SERIAL_BATCH 4
+#endif
+#ifdef NP_CHILD_MAXREG
+#define NP_CHILD_BOUNDS __maxnreg__(NP_CHILD_MAXREG)
+#else
+#define NP_CHILD_BOUNDS __launch_bounds__(1024)
+#endif
+#ifdef NP_PARENT_MAXREG
+#define NP_PARENT_BOUNDS __maxnreg__(NP_PARENT_MAXREG)
+#else
+#define NP_PARENT_BOUNDS __launch_bounds__(kMaxParentBlock)
+#endif
 
 namespace nestpar {
 
@@ -39,23 +67,48 @@ enum Stat : int { S_LEVELS, S_PARENTS, S_SERIAL, S_LAUNCHP, S_DEVLAUNCH, S_AGGGR
 // Device-resident state of one solve. Level L reads frontier buffer L&1 with
 // count[L%3] and appends to buffer (L+1)&1 / count[(L+1)%3]; the parent
 // kernel of level L zeroes count[(L+2)%3], which level L+1 appends to.
-struct LevelState {
-  int level;
-  int max_levels;
-  unsigned long long epoch;      // tags look-back flags; never reused, so flags need no reset
-  int ticket;                    // next parent tile of the running parent grid
-  int parent_done;               // CTAs of the parent grid that finished
-  int child_done;                // CTAs of the stream-ordered child grid that finished
+// base and count[] share one 16-byte word: one load gives L and its size.
+struct __align__(16) LevelState {
+  int base;                      // level of body position 0; changes only between bodies
   int count[3];
-  int agg_records;               // grid-host aggregation: launching parents of this level
-  int agg_blocks;                // grid-host aggregation: coarsened child blocks of this level
+  unsigned long long solve_id;   // look-back epoch of level L: solve_id << 31 | L (never reused)
+  int max_levels;
   unsigned error;
-  unsigned pad;
-  unsigned long long agg_acc;    // grid-host aggregation with the atomic scan: packed totals
+  int ticket[4];                 // slot L % 4: next parent tile of level L
+  int agg_records[4];            // slot L % 4: grid-host totals, look-back scan
+  int agg_blocks[4];
+  unsigned long long agg_acc[4]; // slot L % 4: grid-host totals, atomic scan (parents << 40 | blocks)
   unsigned long long s[S_N];     // counters (np_stats)
   int body_iters;                // conditional-while iterations of this solve (bounded)
-  int pad2;
+  int pad;
 };
+
+__device__ __forceinline__ unsigned long long level_epoch(const LevelState* st, int L) {
+  return (__ldcg(&st->solve_id) << 31) | (unsigned long long)(unsigned)L;
+}
+
+// Level L of a level-mode kernel at body position k, and that level's frontier size.
+__device__ __forceinline__ void level_of(const LevelState* st, int k, int& L, int& count) {
+  const int4 h = __ldcg(reinterpret_cast<const int4*>(st));
+  L = h.x + k;
+  const int m = L % 3;
+  count = m == 0 ? h.y : (m == 1 ? h.z : h.w);
+}
+
+// Run by one thread of the parent grid of level L: clear what level L + 2
+// will use, and count the level.
+__device__ __forceinline__ void level_open(LevelState* st, int L, int count) {
+  const int s2 = (L + 2) & 3;
+  st->ticket[s2] = 0;
+  st->agg_records[s2] = 0;
+  st->agg_blocks[s2] = 0;
+  st->agg_acc[s2] = 0ull;
+  st->count[(L + 2) % 3] = 0;
+  if (count > 0) {
+    atomicAdd(&st->s[S_LEVELS], 1ull);
+    if (L > 0) atomicAdd(&st->s[S_PUSHES], (unsigned long long)count);
+  }
+}
 
 // What a child item needs; passed by value to every child grid.
 struct BodyArgs {
@@ -103,7 +156,8 @@ struct Args {
   int group_blocks;              // 0 = whole grid (grid granularity)
   int agg_threshold;
   int scan;                      // 0 look-back, 1 atomic
-  int advance;                   // 1: the parent grid's last CTA advances the level
+  int k;                         // level mode: position in the graph body (level = base + k)
+  int pad;
 };
 
 struct AggSeg {
@@ -114,10 +168,9 @@ struct AggSeg {
   int nrec;
   int total;
   int mode;                      // 0: fixed segment; 1: grid-host, look-back totals; 2: grid-host, atomic totals
-  int advance;                   // 1: the child grid's last CTA advances the level
+  int k;                         // level mode: position in the graph body
   int level_mode;                // 1: take L, next and next_count from the level state
   int cb;                        // child block size; a CTA hosts blockDim.x / cb child blocks
-  int qchunk;                    // frontier slots a warp reserves at a time (0 = exact appends)
   int pad;
 };
 
@@ -290,20 +343,19 @@ __device__ __forceinline__ int warp_search_near(const int* boff, int lo, int hi,
 // ------------------------------------------------------------ frontier sinks
 //
 // Appends to the next frontier go through a sink. All appends of a level hit
-// one counter, so the sinks keep atomics on it rare:
-//   WarpSink  the 32 lanes of a warp append a batch together: one warp scan of
-//             the per-lane counts, then either one exact reservation per batch
-//             (chunk == 0) or slots from a warp-private run of `chunk` slots
-//             reserved ahead (unused slots are padded with -1 when the warp
-//             finishes, and parents skip -1);
-//   CtaSink   diverged lanes (a parent's serial loop) append into a shared-memory
-//             buffer of the CTA, flushed with one atomic per tile.
+// one counter, so the sinks keep atomics on it rare and frontiers exact (no
+// holes):
+//   StageSink  the 32 lanes of a warp append a batch together into a
+//              shared-memory buffer of the CTA (one shared atomic per warp
+//              batch); the CTA flushes the buffer with one global atomic when it
+//              finishes; what does not fit goes to global memory at once;
+//   CtaSink    the same buffer filled by diverged lanes (the serial loops of the
+//              CTA-tiled parent kernel), flushed once per tile;
+//   WarpSink   one exact reservation per warp batch (device-launched child
+//              grids of one parent, which are too small to stage).
 struct WarpSink {
   int* next;
   int* count;
-  int chunk;
-  int base;
-  int left;
   template <int K>
   __device__ __forceinline__ void push(const bool (&pf)[K], const int (&v)[K]) {
     int c = 0;
@@ -318,44 +370,71 @@ struct WarpSink {
     }
     const int total = __shfl_sync(kFull, inc, 31);
     if (total == 0) return;
-    int r = inc - c;   // rank of this lane's first append within the warp's batch
-    if (chunk == 0) {
-      int b0 = 0;
-      if (lane == 31) b0 = atomicAdd(count, total);
-      b0 = __shfl_sync(kFull, b0, 31);
+    int r = inc - c;
+    int b0 = 0;
+    if (lane == 31) b0 = atomicAdd(count, total);
+    b0 = __shfl_sync(kFull, b0, 31);
 #pragma unroll
-      for (int k = 0; k < K; k++)
-        if (pf[k]) next[b0 + r++] = v[k];
-      return;
+    for (int k = 0; k < K; k++)
+      if (pf[k]) next[b0 + r++] = v[k];
+  }
+};
+
+constexpr int kCtaStage = 2048;   // shared staging slots of a child / warp-tiled parent CTA
+
+struct StageSink {
+  int* next;
+  int* count;
+  int* q;    // shared staging buffer [kCtaStage]
+  int* qn;   // shared fill counter (counts appends beyond the buffer too)
+  template <int K>
+  __device__ __forceinline__ void push(const bool (&pf)[K], const int (&v)[K]) {
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < K; k++) c += pf[k] ? 1 : 0;
+    const int lane = threadIdx.x & 31;
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += x;
     }
-    const int need = total - left;   // appends beyond the current run
-    int nb = 0, nres = 0;
-    if (need > 0) {
-      nres = ceil_div(need, chunk) * chunk;
-      if (lane == 0) nb = atomicAdd(count, nres);
-      nb = __shfl_sync(kFull, nb, 0);
+    const int total = __shfl_sync(kFull, inc, 31);
+    if (total == 0) return;
+    int pos = 0;
+    if (lane == 0) pos = atomicAdd(qn, total);
+    pos = __shfl_sync(kFull, pos, 0);
+    const int fit = max(0, min(total, kCtaStage - pos));   // appends that land in the buffer
+    int gb = 0;
+    if (fit < total) {
+      if (lane == 0) gb = atomicAdd(count, total - fit);
+      gb = __shfl_sync(kFull, gb, 0);
     }
+    int r = inc - c;
 #pragma unroll
     for (int k = 0; k < K; k++) {
       if (pf[k]) {
-        next[r < left ? base + r : nb + (r - left)] = v[k];
+        if (r < fit) q[pos + r] = v[k];
+        else next[gb + (r - fit)] = v[k];
         r++;
       }
     }
-    if (need > 0) {
-      base = nb + need;
-      left = nres - need;
-    } else {
-      base += total;
-      left -= total;
-    }
-  }
-  // pad the unused reserved slots (the next level skips ids < 0)
-  __device__ __forceinline__ void flush() {
-    for (int i = threadIdx.x & 31; i < left; i += 32) next[base + i] = -1;
-    left = 0;
   }
 };
+
+// Run by every thread of the CTA once it is done appending: one atomic on the
+// level counter reserves the staged appends, then the CTA copies them out.
+__device__ __forceinline__ void stage_flush(const int* q, int* qn, int* next, int* count, int* s_base) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int n = min(*qn, kCtaStage);
+    *s_base = n > 0 ? atomicAdd(count, n) : 0;
+    *qn = n;
+  }
+  __syncthreads();
+  const int n = *qn, base = *s_base;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) next[base + i] = q[i];
+}
 
 constexpr int kStageSlots = 1024;   // shared-memory staging slots per parent CTA
 
@@ -528,10 +607,10 @@ struct BezierBody {
 // One coarsened child block: CF consecutive original blocks of one parent
 // (Section IV-B; contiguous original blocks), in batches of up to 8 original
 // blocks whose items are all loaded before any is applied.
-template <class Body, int CF>
+template <class Body, int CF, class Sink>
 __device__ __forceinline__ void run_coarsened(const BodyArgs& b, const typename Body::P& p, int N, int cb, int B,
-                                              int tid, WarpSink& sink) {
-  constexpr int KB = CF < 8 ? CF : 8;
+                                              int tid, Sink& sink) {
+  constexpr int KB = CF < NP_CHILD_BATCH ? CF : NP_CHILD_BATCH;
 #pragma unroll
   for (int k0 = 0; k0 < CF; k0 += KB) {
     if ((cb * CF + k0) * B >= N) break;   // uniform across the block
@@ -555,7 +634,7 @@ __device__ __forceinline__ void run_coarsened(const BodyArgs& b, const typename 
 // form): the parent thread walks its children in order, four at a time.
 template <class Body>
 __device__ __forceinline__ void run_serial(const BodyArgs& b, int pid, int base, int N, CtaSink& sink) {
-  constexpr int KS = 4;
+  constexpr int KS = NP_SERIAL_BATCH;
   const typename Body::P p = Body::parent(b, pid, base, N);
   for (int i0 = 0; i0 < N; i0 += KS) {
     typename Body::F f[KS];
@@ -578,31 +657,11 @@ __device__ __forceinline__ void add_stat(LevelState* st, int k, unsigned long lo
   if (v) atomicAdd(&st->s[k], v);
 }
 
-// Level bookkeeping once a level's grids are done: counters reset, and the
-// level/epoch advance when the level had parents.
-__device__ __forceinline__ void advance_level(LevelState* st) {
-  const int L = st->level;
-  const int c = st->count[L % 3];
-  st->ticket = 0;
-  st->parent_done = 0;
-  st->child_done = 0;
-  st->agg_records = 0;
-  st->agg_blocks = 0;
-  st->agg_acc = 0ull;
-  if (c > 0) {
-    st->s[S_LEVELS] += 1;
-    st->s[S_PUSHES] += (unsigned long long)st->count[(L + 1) % 3];
-    st->level = L + 1;
-    st->epoch += 1;
-  }
-  __threadfence();
-}
-
 // Child grid of one parent (plain CDP, thresholded or coarsened launch).
 template <class Body, int CF>
-__global__ void __launch_bounds__(1024) child_direct(BodyArgs b, int pid, int base, int N) {
+__global__ void NP_CHILD_BOUNDS child_direct(BodyArgs b, int pid, int base, int N) {
   const typename Body::P p = Body::parent(b, pid, base, N);
-  WarpSink sink{b.next, b.next_count, 0, 0, 0};
+  WarpSink sink{b.next, b.next_count};
   run_coarsened<Body, CF>(b, p, N, blockIdx.x, blockDim.x, threadIdx.x, sink);
 }
 
@@ -613,22 +672,29 @@ __global__ void __launch_bounds__(1024) child_direct(BodyArgs b, int pid, int ba
 // memory) each child block takes a contiguous range of aggregated blocks, so
 // after the first search the parent index only moves forward.
 template <class Body, int CF>
-__global__ void __launch_bounds__(1024) child_agg(BodyArgs b, AggSeg s) {
+__global__ void NP_CHILD_BOUNDS child_agg(BodyArgs b, AggSeg s) {
+  __shared__ int s_stage[kCtaStage];
+  __shared__ int s_stage_n, s_stage_base;
+  if (threadIdx.x == 0) s_stage_n = 0;
   int nrec = s.nrec, total = s.total;
   LevelState* st = b.st;
-  if (s.mode == 1) {
-    nrec = __ldcg(&st->agg_records);
-    total = __ldcg(&st->agg_blocks);
-  } else if (s.mode == 2) {
-    const unsigned long long acc = __ldcg(&st->agg_acc);
-    nrec = (int)(acc >> 40);
-    total = (int)(acc & ((1ull << 40) - 1));
-  }
-  if (s.level_mode) {
-    const int L = __ldcg(&st->level);
-    b.L = L;
-    b.next = (L & 1) ? s.fr0 : s.fr1;
-    b.next_count = &st->count[(L + 1) % 3];
+  if (s.mode != 0) {
+    int L = b.L;
+    if (s.level_mode) {
+      L = __ldcg(&st->base) + s.k;
+      b.L = L;
+      b.next = (L & 1) ? s.fr0 : s.fr1;
+      b.next_count = &st->count[(L + 1) % 3];
+    }
+    const int slot = L & 3;
+    if (s.mode == 1) {
+      nrec = __ldcg(&st->agg_records[slot]);
+      total = __ldcg(&st->agg_blocks[slot]);
+    } else {
+      const unsigned long long acc = __ldcg(&st->agg_acc[slot]);
+      nrec = (int)(acc >> 40);
+      total = (int)(acc & ((1ull << 40) - 1));
+    }
   }
   const int cb = s.cb, per_cta = (int)blockDim.x / cb;
   const int sub = (int)blockIdx.x * per_cta + (int)threadIdx.x / cb, stid = (int)threadIdx.x % cb;
@@ -637,7 +703,8 @@ __global__ void __launch_bounds__(1024) child_agg(BodyArgs b, AggSeg s) {
   const int last = min(total, first + chunk);
   int j = -1, next_off = 0, off = 0, N = 0;
   typename Body::P p{};
-  WarpSink sink{b.next, b.next_count, s.qchunk, 0, 0};
+  __syncthreads();
+  StageSink sink{b.next, b.next_count, s_stage, &s_stage_n};
   for (int B0 = first; B0 < last; B0++) {
     if (j < 0 || B0 >= next_off) {
       j = j < 0 ? warp_search(s.boff, 0, nrec, B0) : warp_search_near(s.boff, j + 1, nrec, B0);
@@ -649,22 +716,10 @@ __global__ void __launch_bounds__(1024) child_agg(BodyArgs b, AggSeg s) {
     }
     run_coarsened<Body, CF>(b, p, N, B0 - off, cb, stid, sink);
   }
-  sink.flush();
-  if (s.mode != 0) {
-    // persistent (grid-host) form: count its blocks here; device-launched
-    // grids are counted by the launching parent
-    __syncthreads();
-    if (stid == 0) add_stat(st, S_CBLOCKS, (unsigned long long)max(last - first, 0));
-    if (threadIdx.x == 0) {
-      if (s.advance) {
-        __threadfence();
-        if (atomicAdd(&st->child_done, 1) == (int)gridDim.x - 1) {
-          __threadfence();
-          advance_level(st);
-        }
-      }
-    }
-  }
+  if constexpr (Body::kPushes) stage_flush(s_stage, &s_stage_n, b.next, b.next_count, &s_stage_base);
+  // persistent (grid-host) form: count its blocks here; device-launched
+  // grids are counted by the launching parent
+  if (s.mode != 0 && stid == 0 && last > first) add_stat(st, S_CBLOCKS, (unsigned long long)(last - first));
 }
 
 // --------------------------------------------------------------- parent side
@@ -687,7 +742,7 @@ __device__ __forceinline__ void launch_direct(const BodyArgs& b, int pid, int ba
 template <class Body, int CF>
 __device__ __forceinline__ void launch_aggregated(const BodyArgs& b, const int4* rec, const int* boff, int nrec,
                                                   int total, int child_block, unsigned* s_stat, CtaSink& sink) {
-  AggSeg s{rec, boff, nullptr, nullptr, nrec, total, 0, 0, 0, child_block, 0, 0};
+  AggSeg s{rec, boff, nullptr, nullptr, nrec, total, 0, 0, 0, child_block, 0};   // a fixed segment
   child_agg<Body, CF><<<total, child_block, 0, cudaStreamFireAndForget>>>(b, s);
   if (cudaGetLastError() != cudaSuccess) {
     // run the aggregated grid's work in this thread: parent by parent, serially
@@ -709,13 +764,13 @@ __device__ __forceinline__ void warp_stat(unsigned* s_stat, int k, unsigned v) {
   if ((threadIdx.x & 31) == 0 && t) atomicAdd(&s_stat[k], t);
 }
 
-// The parent kernel of one level. GRAN selects the form; CF is the coarsening
-// factor of the child kernel it launches (device-launch forms only). Per tile:
-// child counts, output offsets (Bezier), the launch decision, the aggregation
-// scan, records and launch; the serial children of the parents below the
-// threshold come last, so no scan ever waits behind a serial loop.
+// The parent kernel of the device-launch forms (CTA tiles). GRAN selects the
+// launch scope; CF is the coarsening factor of the child kernel it launches.
+// Per tile: child counts, output offsets (Bezier), the launch decision, the
+// aggregation scan, records and launch; the serial children of the parents
+// below the threshold come last, so no scan ever waits behind a serial loop.
 template <class Body, int GRAN, int CF>
-__global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
+__global__ void NP_PARENT_BOUNDS parent_kernel(Args a) {
   __shared__ int s_tile;
   __shared__ uint2 s_scan[33];
   __shared__ V3 s_v3;
@@ -725,10 +780,11 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
   const int tid = threadIdx.x, PB = blockDim.x, lane = tid & 31, warp = tid >> 5;
   LevelState* st = a.st;
   const bool fixed = a.count_fixed >= 0;
-  const int L = fixed ? a.L_fixed : __ldcg(&st->level);
-  const unsigned long long epoch = __ldcg(&st->epoch);
-  const int count = fixed ? a.count_fixed : __ldcg(&st->count[L % 3]);
-  if (!fixed && blockIdx.x == 0 && tid == 0) st->count[(L + 2) % 3] = 0;
+  int L = a.L_fixed, count = a.count_fixed;
+  if (!fixed) level_of(st, a.k, L, count);
+  const unsigned long long epoch = level_epoch(st, L);
+  const int slot = L & 3;
+  if (!fixed && blockIdx.x == 0 && tid == 0) level_open(st, L, count);
   if (count <= 0) return;
   const int* ids = fixed ? a.ids : ((L & 1) ? a.fr1 : a.fr0);
   BodyArgs b = a.b;
@@ -737,9 +793,7 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
   b.next_count = fixed ? a.next_count_ovr : &st->count[(L + 1) % 3];
   const int ntiles = ceil_div(count, PB);
   // CTAs beyond the number of tiles have nothing to take: leave at once
-  // (the level's last CTA is then the last of the first min(grid, tiles))
-  const int active = min((int)gridDim.x, ntiles);
-  if ((int)blockIdx.x >= active) return;
+  if ((int)blockIdx.x >= ntiles) return;
   const int T = a.threshold < 1 ? 1 : a.threshold;
   const int CB = a.child_block;
   if (tid < S_N) s_stat[tid] = 0;
@@ -748,7 +802,7 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
 
   for (;;) {
     if (tid == 0) {
-      s_tile = atomicAdd(&st->ticket, 1);
+      s_tile = atomicAdd(&st->ticket[slot], 1);
       s_qn = 0;
     }
     __syncthreads();
@@ -779,12 +833,12 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
         N = 0;
       }
     }
-    const bool launch = GRAN != G_NODP && valid && N >= T;
+    const bool launch = valid && N >= T;
     const bool serial = valid && !launch && N > 0;
     warp_stat(s_stat, S_PARENTS, valid ? 1u : 0u);
     warp_stat(s_stat, S_ITEMS, (unsigned)N);
     warp_stat(s_stat, S_SERIAL, serial ? 1u : 0u);
-    if constexpr (GRAN != G_NODP) {
+    {
       warp_stat(s_stat, S_LAUNCHP, launch ? 1u : 0u);
       warp_stat(s_stat, S_CITEMS, launch ? (unsigned)N : 0u);
       const unsigned cg = launch ? (unsigned)ceil_div(ceil_div(N, CB), a.cfactor) : 0u;
@@ -830,8 +884,8 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
           if (tid == 0 && ta > 0) launch_aggregated<Body, CF>(b, a.rec + seg, a.boff + seg, (int)ta, (int)tb, CB, s_stat, sink);
         }
       } else {
-        // multi-block / grid granularity: the scope is a group of G tiles
-        const int G = (GRAN == G_GRID_HOST || a.group_blocks <= 0) ? ntiles : a.group_blocks;
+        // multi-block / grid-device granularity: the scope is a group of G tiles
+        const int G = a.group_blocks <= 0 ? ntiles : a.group_blocks;
         const int g = tile / G, first = g * G, gsize = min(G, ntiles - first);
         unsigned ea, eb, ta, tb;
         block_scan2(launch ? 1u : 0u, cg, ea, eb, ta, tb, s_scan);
@@ -841,23 +895,17 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
             if (lane == 0) s_v3 = x;
           }
         } else if (tid == 0) {
-          unsigned long long* acc = (GRAN == G_GRID_HOST) ? &st->agg_acc : &a.grp_acc[g];
-          const unsigned long long old = atomicAdd(acc, ((unsigned long long)ta << 40) | tb);
+          const unsigned long long old = atomicAdd(&a.grp_acc[g], ((unsigned long long)ta << 40) | tb);
           s_v3 = V3{(unsigned)(old >> 40), (unsigned)(old & ((1ull << 40) - 1)), 0u};
         }
         __syncthreads();
         const V3 x = s_v3;
-        const int seg = (GRAN == G_GRID_HOST) ? 0 : first * PB;
+        const int seg = first * PB;
         if (launch) {
           a.rec[seg + x.a + ea] = make_int4(pid, base, N, 0);
           a.boff[seg + x.a + ea] = (int)(x.b + eb);
         }
-        if constexpr (GRAN == G_GRID_HOST) {
-          if (a.scan == 0 && tile == ntiles - 1 && tid == 0) {
-            st->agg_records = (int)(x.a + ta);
-            st->agg_blocks = (int)(x.b + tb);
-          }
-        } else {
+        {
           if (a.scan == 0 && tile == first + gsize - 1 && tid == 0) a.grp_total[g] = make_uint2(x.a + ta, x.b + tb);
           __threadfence();
           __syncthreads();
@@ -882,7 +930,7 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
         }
       }
     }
-    // serialised children last (thresholding's fallback; every child in NODP)
+    // serialised children last (thresholding's fallback)
     if (serial) run_serial<Body>(b, pid, base, N, sink);
     __syncthreads();
     if constexpr (Body::kPushes) {
@@ -899,15 +947,142 @@ __global__ void __launch_bounds__(kMaxParentBlock) parent_kernel(Args a) {
 
   __syncthreads();
   if (tid < S_N && tid != S_LEVELS && tid != S_PUSHES) add_stat(st, tid, s_stat[tid]);
-  if (a.advance) {
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      if (atomicAdd(&st->parent_done, 1) == active - 1) {
-        __threadfence();
-        advance_level(st);
+}
+
+// ------------------------------------------------ parent side, warp tiles
+//
+// The parent kernel of the forms without device launches: no dynamic
+// parallelism at all (FORM 0, every parent serialises its children) and
+// grid-host aggregation (FORM 1: parents at or above the threshold are
+// aggregated into the grid the next stream/graph node runs). Each warp takes
+// 32-parent tiles from the level's ticket and works alone: a warp scan and a
+// warp-level decoupled look-back over all tiles of the grid give the records'
+// slots and block offsets, and the serialised children run in a warp-uniform
+// loop (lanes with fewer children idle) that appends through a warp sink. No
+// CTA barrier anywhere, so no warp waits for another warp's serial loop.
+template <class Body, int FORM>
+__global__ void NP_PARENT_BOUNDS parent_warp(Args a) {
+  __shared__ int s_stage[kCtaStage];
+  __shared__ int s_stage_n, s_stage_base;
+  const int lane = threadIdx.x & 31;
+  LevelState* st = a.st;
+  const bool fixed = a.count_fixed >= 0;
+  int L = a.L_fixed, count = a.count_fixed;
+  if (!fixed) level_of(st, a.k, L, count);
+  const int slot = L & 3;
+  if (!fixed && blockIdx.x == 0 && threadIdx.x == 0) level_open(st, L, count);
+  if (count <= 0) return;   // uniform over the grid
+  const int ntiles = ceil_div(count, 32);
+  // CTAs whose warps would all find no tile leave at once
+  if ((int)blockIdx.x * ((int)blockDim.x >> 5) >= ntiles) return;
+  if (threadIdx.x == 0) s_stage_n = 0;
+  __syncthreads();
+  const unsigned long long epoch = level_epoch(st, L);
+  const int* ids = fixed ? a.ids : ((L & 1) ? a.fr1 : a.fr0);
+  BodyArgs b = a.b;
+  b.L = L;
+  b.next = fixed ? a.next_ovr : ((L & 1) ? a.fr0 : a.fr1);
+  b.next_count = fixed ? a.next_count_ovr : &st->count[(L + 1) % 3];
+  const int T = a.threshold < 1 ? 1 : a.threshold;
+  const int CB = a.child_block;
+  StageSink sink{b.next, b.next_count, s_stage, &s_stage_n};
+  unsigned long long n_par = 0, n_items = 0, n_serial = 0, n_launch = 0, n_citems = 0;
+
+  for (;;) {
+    int tile = 0;
+    if (lane == 0) tile = atomicAdd(&st->ticket[slot], 1);
+    tile = __shfl_sync(kFull, tile, 0);
+    if (tile >= ntiles) break;
+    const int i = tile * 32 + lane;
+    int pid = 0, base = 0, N = 0;
+    if (i < count) pid = ids ? __ldcg(&ids[i]) : i;
+    const bool valid = i < count && pid >= 0;   // frontier slots padded with -1 hold no parent
+    if (valid) Body::count(a, pid, base, N);
+    if constexpr (Body::kOffsets) {
+      // output offsets: exclusive scan of N over all parents, in parent order
+      int inc = N;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += x;
+      }
+      const unsigned t0 = (unsigned)__shfl_sync(kFull, inc, 31);
+      const V3 x = lookback(a.ob_flag, a.ob_agg, a.ob_incl, tile, 0, epoch, V3{t0, 0u, 0u}, st);
+      base = (int)(x.a + (unsigned)(inc - N));
+      if (valid) a.offsets[i] = base;
+      if (tile == ntiles - 1 && lane == 0) a.offsets[count] = (int)(x.a + t0);
+      if (valid && (long long)base + N > a.cap) {
+        atomicOr(&st->error, kErrCapacity);
+        N = 0;
       }
     }
+    const bool launch = FORM == 1 && valid && N >= T;
+    const bool serial = valid && !launch && N > 0;
+    n_par += __popc(__ballot_sync(kFull, valid));
+    n_items += __reduce_add_sync(kFull, (unsigned)N);
+    n_serial += __popc(__ballot_sync(kFull, serial));
+    if constexpr (FORM == 1) {
+      const unsigned lm = __ballot_sync(kFull, launch);
+      n_launch += __popc(lm);
+      n_citems += __reduce_add_sync(kFull, launch ? (unsigned)N : 0u);
+      const unsigned cg = launch ? (unsigned)ceil_div(ceil_div(N, CB), a.cfactor) : 0u;
+      unsigned inc = cg;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned x = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += x;
+      }
+      const unsigned ta = __popc(lm), tb = __shfl_sync(kFull, inc, 31);
+      const unsigned ea = __popc(lm & lanemask_lt()), eb = inc - cg;
+      V3 x{0u, 0u, 0u};
+      if (a.scan == 0) {
+        x = lookback(a.lb_flag, a.lb_agg, a.lb_incl, tile, 0, epoch, V3{ta, tb, 0u}, st);
+      } else {
+        unsigned long long old = 0ull;
+        if (lane == 0) old = atomicAdd(&st->agg_acc[slot], ((unsigned long long)ta << 40) | tb);
+        old = __shfl_sync(kFull, old, 0);
+        x = V3{(unsigned)(old >> 40), (unsigned)(old & ((1ull << 40) - 1)), 0u};
+      }
+      if (launch) {
+        a.rec[x.a + ea] = make_int4(pid, base, N, 0);
+        a.boff[x.a + ea] = (int)(x.b + eb);
+      }
+      if (a.scan == 0 && tile == ntiles - 1 && lane == 0) {
+        st->agg_records[slot] = (int)(x.a + ta);
+        st->agg_blocks[slot] = (int)(x.b + tb);
+      }
+    }
+    // serialised children, warp-uniform: lane l walks its own parent's
+    // children in order; lanes with fewer (or none) idle through the tail
+    const int myN = serial ? N : 0;
+    const int maxN = (int)__reduce_max_sync(kFull, (unsigned)myN);
+    if (maxN > 0) {
+      constexpr int KS = NP_SERIAL_BATCH;
+      const typename Body::P p = Body::parent(b, valid ? pid : 0, base, N);
+      for (int i0 = 0; i0 < maxN; i0 += KS) {
+        typename Body::F f[KS];
+        bool v[KS];
+        int idx[KS];
+#pragma unroll
+        for (int k = 0; k < KS; k++) {
+          idx[k] = i0 + k;
+          v[k] = idx[k] < myN;
+          f[k] = v[k] ? Body::fetch(b, p, idx[k]) : typename Body::F{};
+        }
+        bool pf[KS];
+        int pv[KS];
+        Body::template apply_batch<KS>(b, p, idx, f, v, pf, pv);
+        if constexpr (Body::kPushes) sink.template push<KS>(pf, pv);
+      }
+    }
+  }
+  if constexpr (Body::kPushes) stage_flush(s_stage, &s_stage_n, b.next, b.next_count, &s_stage_base);
+  if (lane == 0) {
+    add_stat(st, S_PARENTS, n_par);
+    add_stat(st, S_ITEMS, n_items);
+    add_stat(st, S_SERIAL, n_serial);
+    add_stat(st, S_LAUNCHP, n_launch);
+    add_stat(st, S_CITEMS, n_citems);
   }
 }
 

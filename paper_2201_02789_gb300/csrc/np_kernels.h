@@ -16,8 +16,8 @@ inline int cf_index(int cf) {
 }
 
 struct BodyKernels {
-  const void* parent_nodp;                    // parent_kernel<Body, G_NODP, 1>
-  const void* parent_grid_host;               // parent_kernel<Body, G_GRID_HOST, 1>
+  const void* parent_nodp;                    // parent_warp<Body, 0>
+  const void* parent_grid_host;               // parent_warp<Body, 1>
   const void* parent[4][kNumCF];              // [NONE, WARP, BLOCK, MULTIBLOCK/GRID_DEVICE][cf]
   const void* child_direct[kNumCF];
   const void* child_agg[kNumCF];

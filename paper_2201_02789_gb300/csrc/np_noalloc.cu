@@ -51,14 +51,14 @@ DeviceScratch g_devices[kMaxDevices];
 // Per-call reset of what must start at zero (the epoch only grows, so the
 // look-back flags of earlier calls never match a later call).
 __global__ void noalloc_reset_kernel(LevelState* st) {
-  st->epoch += 1;
+  st->solve_id += 1;
   st->body_iters = 0;
-  st->ticket = 0;
-  st->parent_done = 0;
-  st->child_done = 0;
-  st->agg_records = 0;
-  st->agg_blocks = 0;
-  st->agg_acc = 0ull;
+  for (int k = 0; k < 4; k++) {
+    st->ticket[k] = 0;
+    st->agg_records[k] = 0;
+    st->agg_blocks[k] = 0;
+    st->agg_acc[k] = 0ull;
+  }
   st->error = 0u;
   for (int k = 0; k < S_N; k++) st->s[k] = 0ull;
 }

@@ -15,7 +15,8 @@ import threading
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libnestpar.so")
+# NESTPAR_LIB selects another build of the same library (tuning variants)
+LIB_PATH = os.environ.get("NESTPAR_LIB") or os.path.join(_PKG, "_build", "libnestpar.so")
 
 NP_OK, NP_ERR_INVALID, NP_ERR_CUDA, NP_ERR_NOMEM, NP_ERR_CAPACITY, NP_ERR_LAUNCH, NP_ERR_TIMEOUT, \
     NP_ERR_UNSUPPORTED = range(8)

@@ -333,3 +333,20 @@ def test_bt64k_full(ctx):
     np.testing.assert_array_equal(off, ref_off)
     ok, worst = bezier_tolerance_ok(pts, ref_pts)
     assert ok, worst
+
+
+# ------------------------------------------------------------------ stress
+
+@pytest.mark.parametrize("scan", [npb.NP_SCAN_LOOKBACK, npb.NP_SCAN_ATOMIC], ids=["lookback", "atomic"])
+def test_multiblock_repeated_runs(ctx, scan):
+    """Group counters and accumulators are reset by each group's last block;
+    repeated solves on alternating graphs and group sizes must stay exact."""
+    graphs = [gen.bfs4k(), gen.rmat(13, 12, seed=23)]
+    devs = [DevGraph(g) for g in graphs]
+    refs = [(oracle.bfs(g.row_ptr, g.col, 0), oracle.sssp(g.row_ptr, g.col, g.w, 0)) for g in graphs]
+    for rep in range(6):
+        for gi, (dg, (rl, rd)) in enumerate(zip(devs, refs)):
+            cfg = npb.config("tca", granularity="multiblock", group_blocks=1 + (rep + gi) % 4, scan=scan,
+                             threshold=[8, 32, 128][rep % 3], child_block=[32, 256][gi])
+            np.testing.assert_array_equal(bfs(ctx, dg, 0, cfg), rl)
+            np.testing.assert_array_equal(sssp(ctx, dg, 0, cfg), rd)
