@@ -370,7 +370,7 @@ def run_ours(args, ws, rank, local):
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": CONFIG,
-            "form": "threshold 32 + coarsening 8 (32-thread child blocks) + grid aggregation (look-back scan), "
+            "form": "threshold 32 + coarsening 8 (32-thread child blocks) + grid aggregation (atomic scan), "
                     "while-graph level loop",
             "ms_per_solve": {"median": statistics.median(ms), "min": min(ms)},
             "edges_reached": mr, "levels": st["levels"], "relaxations": st["items"],

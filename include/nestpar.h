@@ -102,9 +102,11 @@ typedef struct np_config {
 } np_config;
 
 /* Fills the library defaults: CDP, threshold 32, cfactor 8, grid-host
- * aggregation, look-back scan, child block 32, parent block 256, AUTO driver
- * (the best of a threshold x cfactor x child-block sweep of BFS and SSSP on an
- * R-MAT scale-20 graph on GB300). */
+ * aggregation, atomic scan, child block 32, parent block 256, AUTO driver
+ * (the best of a threshold x cfactor x child-block x scan sweep of BFS and SSSP
+ * on an R-MAT scale-20 graph on GB300; the look-back scan, which keeps records
+ * in parent order, is selectable and slower there because it publishes and
+ * polls a fenced flag per 32-parent tile). */
 np_status np_config_default(np_config *cfg);
 
 /* ---- problem descriptions ---- */

@@ -714,7 +714,7 @@ np_status np_config_default(np_config* cfg) {
   cfg->agg_threshold = 0;
   cfg->child_block = 32;
   cfg->parent_block = 256;
-  cfg->scan = NP_SCAN_LOOKBACK;
+  cfg->scan = NP_SCAN_ATOMIC;
   cfg->driver = NP_DRIVER_AUTO;
   cfg->unroll = 4;
   cfg->parent_grid = 0;

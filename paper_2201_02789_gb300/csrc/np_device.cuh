@@ -39,7 +39,7 @@
 #define NP_CHILD_BATCH 8
 #endif
 #ifndef NP_SERIAL_BATCH
-#define NP_SERIAL_BATCH 4
+#define NP_SERIAL_BATCH 8
 #endif
 #ifdef NP_CHILD_MAXREG
 #define NP_CHILD_BOUNDS __maxnreg__(NP_CHILD_MAXREG)

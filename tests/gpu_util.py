@@ -56,8 +56,11 @@ def form_grid():
              ("mb8", npb.NP_GRAN_MULTIBLOCK, {"group_blocks": 8}),
              ("griddev", npb.NP_GRAN_GRID_DEVICE, {}), ("gridhost", npb.NP_GRAN_GRID_HOST, {})]
     for gname, gran, extra in grans:
-        for T in (0, 1, 32, 128, 1024, npb.INT32_MAX):
-            for cf in (1, 2, 4, 8, 16):
-                out.append((f"{gname}-T{T}-C{cf}",
-                            npb.config("tca", granularity=gran, threshold=T, cfactor=cf, **extra)))
+        scans = ([("", npb.NP_SCAN_ATOMIC), ("-lb", npb.NP_SCAN_LOOKBACK)]
+                 if gran in (npb.NP_GRAN_MULTIBLOCK, npb.NP_GRAN_GRID_DEVICE, npb.NP_GRAN_GRID_HOST) else [("", npb.NP_SCAN_ATOMIC)])
+        for sname, scan in scans:
+            for T in (0, 1, 32, 128, 1024, npb.INT32_MAX):
+                for cf in (1, 2, 4, 8, 16):
+                    out.append((f"{gname}{sname}-T{T}-C{cf}",
+                                npb.config("tca", granularity=gran, threshold=T, cfactor=cf, scan=scan, **extra)))
     return out
