@@ -1,18 +1,25 @@
 """Benchmark of the nested-parallel hot path on one GB300 (or N replicas).
 
-Workload: single-source shortest paths by frontier Bellman-Ford on a seeded
-R-MAT graph, scale 20 (1,048,576 vertices), edge factor 16 (16,777,216 edges),
-a,b,c,d = .57/.19/.19/.05, uint32 weights uniform in [1, 255], source 0. One
-step = one whole solve (every level of the nested parent/child work) through
-the C ABI, graph resident in HBM. Between timed steps L2 is flushed (a 512 MB
-write) outside the timed events.
+Default workload (the headline): single-source shortest paths by frontier
+Bellman-Ford on a seeded R-MAT graph, scale 20 (1,048,576 vertices), edge
+factor 16 (16,777,216 edges), a,b,c,d = .57/.19/.19/.05, uint32 weights uniform
+in [1, 255], source 0. One step = one whole solve (every level of the nested
+parent/child work) through the C ABI, graph resident in HBM. Between timed
+steps L2 is flushed (a 512 MB write) outside the timed events.
 
-The headline is the aggregated form (threshold + coarsening + grid aggregation);
-plain CDP (one device launch per parent) and the no-dynamic-parallelism form
-are timed beside it on the same GPU. GTEPS = edges out of reached vertices /
-solve time (Graph500 convention).
+The headline is the aggregated form (threshold + coarsening + grid
+aggregation); plain CDP (one device launch per parent), the no-dynamic-
+parallelism form and the device-launch aggregation forms are timed beside it
+on the same GPU. GTEPS = edges out of reached vertices / solve time (Graph500
+convention).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Other workloads (--workload): bfs-rmat20 (BFS on the same graph), bfs4k (the
+4096-vertex power-law digraph), road (a 264K-vertex grid road graph with
+out-degree <= 8: the low-nested-parallelism case, with the never-taken launch
+site measured against the same kernel without it), bt64k (Bezier tessellation
+of 65,536 curves, points/s).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 """
 from __future__ import annotations
 
@@ -33,10 +40,23 @@ sys.path.insert(0, os.path.join(ROOT, "tests"))
 import numpy as np  # noqa: E402
 
 METRIC = "GTEPS and ms/solve at 1 GB300: aggregated form vs plain CDP; % HBM roofline"
-WORKLOAD = "sssp-rmat20"
-CONFIG = {"workload": "sssp_frontier_bellman_ford_rmat_scale20", "vertices": 1 << 20, "edges": 16 << 20,
-          "rmat_abcd": [0.57, 0.19, 0.19, 0.05], "weights": "uint32 uniform [1,255]", "source": 0,
-          "seed": 2, "l2": "flushed between timed steps (512 MB write)"}
+L2_NOTE = "flushed between timed steps (512 MB write)"
+RMAT = {"vertices": 1 << 20, "edges": 16 << 20, "rmat_abcd": [0.57, 0.19, 0.19, 0.05],
+        "weights": "uint32 uniform [1,255]", "source": 0, "seed": 2}
+WORKLOADS = {
+    "sssp-rmat20": dict(kind="sssp", graph="rmat20",
+                        config=dict(workload="sssp_frontier_bellman_ford_rmat_scale20", **RMAT)),
+    "bfs-rmat20": dict(kind="bfs", graph="rmat20", config=dict(workload="bfs_rmat_scale20", **RMAT)),
+    "bfs4k": dict(kind="bfs", graph="bfs4k",
+                  config=dict(workload="bfs_zipf_digraph_4096", vertices=4096, degrees="Zipf(2.1) on [1,1024]",
+                              source=0, seed=1)),
+    "road": dict(kind="sssp", graph="road",
+                 config=dict(workload="sssp_road_grid_264k", vertices=514 * 514, degrees="2..8 (grid, diagonals p=1/2)",
+                             weights="uint32 uniform [1,255]", source=0, seed=6)),
+    "bt64k": dict(kind="bezier", graph=None,
+                  config=dict(workload="bezier_tessellation_65536_curves", curves=65536,
+                              points="ceil(sqrt(kappa)*64) clamped to [4,4096]", seed=3)),
+}
 
 
 def log(*a):
@@ -50,14 +70,14 @@ def dist_env():
     return ws, rank, local
 
 
-def load_graph():
+def _cached(name, make):
     from paper_2201_02789_gb300 import gen
     cache = os.path.join(ROOT, "_cache")
-    path = os.path.join(cache, "rmat20_seed2.npz")
+    path = os.path.join(cache, name + ".npz")
     if os.path.exists(path):
         z = np.load(path)
         return gen.Csr(int(z["n"]), z["row_ptr"], z["col"], z["w"])
-    g = gen.rmat20()
+    g = make()
     try:
         os.makedirs(cache, exist_ok=True)
         np.savez(path + ".tmp.npz", n=g.n, row_ptr=g.row_ptr, col=g.col, w=g.w)
@@ -67,9 +87,36 @@ def load_graph():
     return g
 
 
-def reached_edges(g, dist) -> int:
-    reached = np.asarray(dist) != 0xFFFFFFFF
-    return int(np.diff(g.row_ptr.astype(np.int64))[reached].sum())
+def load_graph(which: str = "rmat20"):
+    from paper_2201_02789_gb300 import gen
+    if which == "rmat20":
+        return _cached("rmat20_seed2", gen.rmat20)
+    if which == "bfs4k":
+        return gen.bfs4k()
+    if which == "road":
+        return _cached("road514_seed6", lambda: gen.road_grid(514, 514, seed=6))
+    raise ValueError(which)
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest value of x over the ranks of the job (x itself on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, units_per_step: int, max_total_ms: float) -> float:
+    """Whole-job throughput in G-units/s: every rank processed `steps` solves of
+    `units_per_step` units (replicas, weak scaling) within the slowest rank's time."""
+    return world * steps * units_per_step / (max_total_ms * 1e-3) / 1e9
+
+
+def reached_edges(g, reached_mask) -> int:
+    return int(np.diff(g.row_ptr.astype(np.int64))[np.asarray(reached_mask)].sum())
 
 
 # ------------------------------------------------------------------- clocks
@@ -145,10 +192,10 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str) -> float | None:
+def ncu_traffic(kernel: str, workload: str) -> float | None:
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was
     taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{WORKLOAD}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         text = open(path).read()
     except OSError:
@@ -162,45 +209,76 @@ def ncu_traffic(kernel: str) -> float | None:
         return None
 
 
-def sssp_kernel_bytes(st: dict) -> dict:
-    """Algorithmic bytes of the SSSP path, split by kernel.
+def kernel_bytes(kind: str, st: dict) -> dict:
+    """Algorithmic bytes of one solve, split by kernel (per the counters `st`).
 
-    Parent grid: per frontier pop the id, the row_ptr pair and dist[u] (16 B);
-    per serialised relaxation col + w + dist[v] (12 B); per launching parent a
-    16 B record and a 4 B block offset; per frontier append 4 B.
-    Child grid: per relaxation col + w + dist[v] (12 B); per launching parent the
-    record, offset and dist[u] it reads back (24 B)."""
-    serial_items = st["items"] - st["child_items"]
-    parent = 16 * st["parents"] + 12 * serial_items + 20 * st["launch_parents"] + 4 * st["pushes"]
-    child = 12 * st["child_items"] + 24 * st["launch_parents"]
-    return {"parent": parent, "child": child, "solve": 16 * st["parents"] + 12 * st["items"]}
+    SSSP parent grid: per frontier pop the id, the row_ptr pair and dist[u]
+    (16 B); per serialised relaxation col + w + dist[v] (12 B); per launching
+    parent a 16 B record and a 4 B block offset; per frontier append 4 B.
+    SSSP child grid: per relaxation 12 B; per launching parent the record,
+    offset and dist[u] it reads back (24 B).
+    BFS: as SSSP without weights and dist[u] (pop 12 B, item 8 B, record read
+    back 20 B). Bezier parent: per curve its control points and offset
+    (28 B), per serialised point 8 B, per launching curve a 20 B record;
+    Bezier child: 8 B per point, 44 B per launching curve (record, offset,
+    control points)."""
+    serial = st["items"] - st["child_items"]
+    if kind == "sssp":
+        parent = 16 * st["parents"] + 12 * serial + 20 * st["launch_parents"] + 4 * st["pushes"]
+        child = 12 * st["child_items"] + 24 * st["launch_parents"]
+        solve = 16 * st["parents"] + 12 * st["items"]
+    elif kind == "bfs":
+        parent = 12 * st["parents"] + 8 * serial + 20 * st["launch_parents"] + 4 * st["pushes"]
+        child = 8 * st["child_items"] + 20 * st["launch_parents"]
+        solve = 20 * st["parents"] + 8 * st["items"]
+    else:
+        parent = 28 * st["parents"] + 8 * serial + 20 * st["launch_parents"]
+        child = 8 * st["child_items"] + 44 * st["launch_parents"]
+        solve = 28 * st["parents"] + 8 * st["items"]
+    return {"parent": parent, "child": child, "solve": solve}
 
 
 # ------------------------------------------------------------------ arms
 
 def run_reference(args, ws, rank):
-    """The oracle (serial Dijkstra) on the host cores, as the reference arm."""
+    """The oracle on the host cores, as the reference arm."""
     if rank != 0:
         return
     import oracle
-    g = load_graph()
+    wl = WORKLOADS[args.workload]
+    if wl["kind"] == "bezier":
+        from paper_2201_02789_gb300 import gen
+        ctrl = gen.bt64k()
+        run = lambda: oracle.bezier(ctrl)
+        units = lambda out: int(out[0][-1])
+        unit = "Gpoints/s"
+    else:
+        g = load_graph(wl["graph"])
+        if wl["kind"] == "sssp":
+            run = lambda: oracle.sssp(g.row_ptr, g.col, g.w, 0)
+            units = lambda d: reached_edges(g, d != 0xFFFFFFFF)
+        else:
+            run = lambda: oracle.bfs(g.row_ptr, g.col, 0)
+            units = lambda lv: reached_edges(g, lv >= 0)
+        unit = "GTEPS"
     for _ in range(args.warmup):
-        d = oracle.sssp(g.row_ptr, g.col, g.w, 0)
+        out = run()
     ts = []
     for _ in range(args.steps):
         t = time.perf_counter()
-        d = oracle.sssp(g.row_ptr, g.col, g.w, 0)
+        out = run()
         ts.append(time.perf_counter() - t)
-    mr = reached_edges(g, d)
+    u = units(out)
     total = sum(ts)
-    value = args.steps * mr / total / 1e9
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": CONFIG,
-            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full Dijkstra solves of the workload"},
-            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    value = args.steps * u / total / 1e9
+    line = {"impl": "reference", "metric": METRIC if args.workload == "sssp-rmat20" else f"{unit} ({args.workload})",
+            "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if wl["kind"] == "bezier" else "u32", "data": "synthetic",
+            "config": dict(wl["config"], l2="n/a (host)"),
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full solves of the workload"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -219,11 +297,130 @@ def time_solves(fn, steps, flush, stream):
     return ms
 
 
+class GraphWorkload:
+    """BFS / SSSP on a resident CSR graph through np_bfs / np_sssp."""
+
+    def __init__(self, kind, g, dev, stream, ctx):
+        import torch
+        from gpu_util import DevGraph
+        from paper_2201_02789_gb300 import nestpar as npb
+        self.npb, self.kind, self.g, self.stream, self.ctx = npb, kind, g, stream, ctx
+        self.dg = DevGraph(g, device=dev)
+        self.out = torch.empty(g.n, dtype=torch.int32, device=dev)
+        self.unit = "GTEPS"
+
+    def solve(self, cfg, stats=False):
+        f = self.npb.np_sssp if self.kind == "sssp" else self.npb.np_bfs
+        return f(self.ctx.handle, self.dg.csr, 0, self.out, cfg, stream=self.stream, stats=stats)
+
+    def result(self):
+        r = self.out.cpu().numpy()
+        return r.view(np.uint32) if self.kind == "sssp" else r
+
+    def reached(self, r):
+        return (r != 0xFFFFFFFF) if self.kind == "sssp" else (r >= 0)
+
+    def units(self):
+        return reached_edges(self.g, self.reached(self.result()))
+
+    def oracle(self):
+        import oracle
+        g = self.g
+        return oracle.sssp(g.row_ptr, g.col, g.w, 0) if self.kind == "sssp" else oracle.bfs(g.row_ptr, g.col, 0)
+
+    def e2e(self, cfg, steps, flush, dev):
+        import torch
+        g = self.g
+        rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+        col_h = torch.from_numpy(g.col).pin_memory()
+        out_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        w_h = torch.from_numpy(g.w.view(np.int32)).pin_memory() if self.kind == "sssp" else None
+        ms = []
+        for k in range(steps + 1):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            if self.kind == "sssp":
+                self.npb.np_sssp_host(self.ctx.handle, rp_h, col_h, w_h, 0, out_h, cfg, stream=self.stream)
+            else:
+                self.npb.np_bfs_host(self.ctx.handle, rp_h, col_h, 0, out_h, cfg, stream=self.stream)
+            if k:
+                ms.append((time.perf_counter() - t) * 1e3)
+        res = out_h.numpy().view(np.uint32) if self.kind == "sssp" else out_h.numpy().copy()
+        h2d = 4 * (g.n + 1) + (8 if self.kind == "sssp" else 4) * g.m
+        return ms, h2d, 4 * g.n, res
+
+
+class BezierWorkload:
+    """Tessellation of the 64K-curve set through np_bezier."""
+
+    def __init__(self, dev, stream, ctx):
+        import torch
+        from paper_2201_02789_gb300 import gen
+        from paper_2201_02789_gb300 import nestpar as npb
+        self.npb, self.stream, self.ctx, self.kind = npb, stream, ctx, "bezier"
+        self.ctrl = gen.bt64k()
+        self.c_d = torch.from_numpy(self.ctrl).to(dev)
+        self.cap = 65536 * 200
+        self.off = torch.empty(65537, dtype=torch.int32, device=dev)
+        self.pts = torch.empty((self.cap, 2), dtype=torch.float32, device=dev)
+        self.unit = "Gpoints/s"
+
+    def solve(self, cfg, stats=False):
+        return self.npb.np_bezier(self.ctx.handle, self.c_d, 65536, self.off, self.pts, self.cap, cfg,
+                                  stream=self.stream, stats=stats)
+
+    def result(self):
+        return self.off.cpu().numpy()
+
+    def units(self):
+        return int(self.result()[-1])
+
+    def oracle(self):
+        import oracle
+        return oracle.bezier_offsets(self.ctrl)
+
+    def e2e(self, cfg, steps, flush, dev):
+        import torch
+        c_h = torch.from_numpy(self.ctrl).pin_memory()
+        off_h = torch.empty(65537, dtype=torch.int32).pin_memory()
+        pts_h = torch.empty((self.cap, 2), dtype=torch.float32).pin_memory()
+        ms = []
+        for k in range(steps + 1):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            self.npb.np_bezier_host(self.ctx.handle, c_h, 65536, off_h, pts_h, self.cap, cfg, stream=self.stream)
+            if k:
+                ms.append((time.perf_counter() - t) * 1e3)
+        total = int(off_h[-1].item())
+        return ms, 24 * 65536, 4 * 65537 + 8 * total, off_h.numpy().copy()
+
+
+def comparison_forms(npb, workload: str, cdp_steps: int):
+    """(name, config, timed steps) of the forms timed beside the headline."""
+    if workload == "road":
+        # low nested parallelism (Section VII-D): no-DP, the same CTA-tiled kernel
+        # with and without a launch site that never runs, and the aggregated form
+        # the pair below differs only in the launch site: same CTA-tiled kernel,
+        # same host-replayed chunk driver
+        chunk = dict(driver=npb.NP_DRIVER_CHUNK)
+        return [("nodp", npb.config("nodp"), 5),
+                ("nodp_cta_tiles_no_launch_code", npb.config("nodp", granularity="none", **chunk), 5),
+                ("cdp_threshold_above_max_degree", npb.config("cdp", threshold=npb.INT32_MAX, **chunk), 5),
+                ("plain_cdp", npb.config("cdp"), cdp_steps),
+                ("t_c", npb.config("tc"), cdp_steps)]
+    return [("plain_cdp", npb.config("cdp"), cdp_steps), ("nodp", npb.config("nodp"), cdp_steps),
+            ("t_c", npb.config("tc"), cdp_steps),
+            ("t_c_a_multiblock", npb.config("tca", granularity="multiblock", group_blocks=8), 5),
+            ("t_c_a_grid_device", npb.config("tca", granularity="grid_device"), 5),
+            ("t_c_a_block", npb.config("tca", granularity="block"), 5)]
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_2201_02789_gb300 import build as nbuild
     from paper_2201_02789_gb300 import nestpar as npb
-    from gpu_util import DevGraph
 
     nbuild.build()
     torch.cuda.set_device(local)
@@ -232,22 +429,21 @@ def run_ours(args, ws, rank, local):
     if distributed:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    g = load_graph()
-    dg = DevGraph(g, device=dev)
+    wl = WORKLOADS[args.workload]
     ctx = npb.Context(local)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 << 20, dtype=torch.int8, device=dev)
-    dist_t = torch.empty(g.n, dtype=torch.int32, device=dev)
+    if wl["kind"] == "bezier":
+        W = BezierWorkload(dev, stream, ctx)
+    else:
+        W = GraphWorkload(wl["kind"], load_graph(wl["graph"]), dev, stream, ctx)
     cfg = npb.config("tca")
 
-    def solve(c=cfg):
-        npb.np_sssp(ctx.handle, dg.csr, 0, dist_t, c, stream=stream)
-
     for _ in range(max(args.warmup, 3)):
-        solve()
-    _, st = npb.np_sssp(ctx.handle, dg.csr, 0, dist_t, cfg, stream=stream, stats=True)
-    d_gpu = dist_t.cpu().numpy().view(np.uint32)
-    mr = reached_edges(g, d_gpu)
+        W.solve(cfg)
+    _, st = W.solve(cfg, stats=True)
+    res_gpu = W.result()
+    units = W.units()
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -255,53 +451,55 @@ def run_ours(args, ws, rank, local):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     sampler.mark("t0")
-    ms = time_solves(solve, args.steps, flush, stream)
+    ms = time_solves(lambda: W.solve(cfg), args.steps, flush, stream)
     torch.cuda.synchronize(dev)
     sampler.mark("t1")
     if distributed:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    total_ms = sum(ms)
-    if distributed:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * args.steps * mr / (total_ms * 1e-3) / 1e9
+    total_ms = max_over_ranks(sum(ms), dev)
+    value = job_value(ws, args.steps, units, total_ms)
     ms_per_step = total_ms / args.steps
 
     if rank != 0:
+        ctx.close()
         if distributed:
             torch.distributed.destroy_process_group()
         return
 
-    # kernels launched per solve (while driver): init + per body iteration
-    # `unroll` x (parent, child) + the condition kernel
-    per_solve = 1 + st["graph_iterations"] * (2 * cfg.unroll + 1)
+    # kernels launched per solve: graph solves launch init + per while-body
+    # iteration `unroll` x (parent, child) + the condition kernel; a
+    # tessellation launches init, parent and child
+    if wl["kind"] == "bezier":
+        per_solve = 3
+    else:
+        per_solve = 1 + st["graph_iterations"] * (2 * cfg.unroll + 1)
     gpu_launches = int(per_solve * args.steps)
+    metric = METRIC if args.workload == "sssp-rmat20" else \
+        f"{W.unit} and ms/solve ({args.workload}): aggregated form vs plain CDP; % HBM roofline"
 
     if args.only_headline:
         # small run for profiler captures: the headline form, then profile-mode solves
         npb.np_profile_enable(ctx.handle, True)
         for _ in range(3):
             flush.zero_()
-            npb.np_sssp(ctx.handle, dg.csr, 0, dist_t, cfg, stream=stream, stats=True)
+            W.solve(cfg, stats=True)
         npb.np_profile_enable(ctx.handle, False)
-        print(json.dumps({"metric": METRIC, "value": value, "unit": "GTEPS", "ms_per_step": ms_per_step,
+        print(json.dumps({"metric": metric, "value": value, "unit": W.unit, "ms_per_step": ms_per_step,
                           "gpu_launches": gpu_launches, "only_headline": True}), flush=True)
         ctx.close()
         return
 
     # forms beside the headline, same GPU, same input
     forms = {}
-    for name, c, reps in (("plain_cdp", npb.config("cdp"), args.cdp_steps),
-                          ("nodp", npb.config("nodp"), args.cdp_steps),
-                          ("t_c", npb.config("tc"), args.cdp_steps),
-                          ("t_c_a_multiblock", npb.config("tca", granularity="multiblock", group_blocks=8), 5),
-                          ("t_c_a_grid_device", npb.config("tca", granularity="grid_device"), 5)):
-        solve(c)
-        t = time_solves(lambda c=c: solve(c), reps, flush, stream)
+    for name, c, reps in comparison_forms(npb, args.workload, args.cdp_steps):
+        W.solve(c)
+        t = time_solves(lambda c=c: W.solve(c), reps, flush, stream)
         m = statistics.median(t)
-        forms[name] = {"ms_per_solve": m, "gteps": mr / (m * 1e-3) / 1e9}
+        _, fst = W.solve(c, stats=True)
+        forms[name] = {"ms_per_solve": m, "value": units / (m * 1e-3) / 1e9, "unit": W.unit,
+                       "device_launches": fst["device_launches"],
+                       "matches_headline": bool(np.array_equal(W.result(), res_gpu))}
     torch.cuda.synchronize(dev)
 
     # roofline of the dominant kernel: profile mode (separate launches, CUDA events)
@@ -310,75 +508,66 @@ def run_ours(args, ws, rank, local):
     prof_runs = 3
     for _ in range(prof_runs):
         flush.zero_()
-        _, pst = npb.np_sssp(ctx.handle, dg.csr, 0, dist_t, cfg, stream=stream, stats=True)
+        _, pst = W.solve(cfg, stats=True)
     prof = npb.np_profile_read(ctx.handle, reset=True)
     npb.np_profile_enable(ctx.handle, False)
-    kb = sssp_kernel_bytes(pst)
+    kb = kernel_bytes(wl["kind"], pst)
     peak, peak_kind = hbm_peak()
     kernels = {"child_agg": (prof["child_ms"], prof["child_launches"], kb["child"]),
-               "parent_kernel": (prof["parent_ms"], prof["parent_launches"], kb["parent"])}
+               "parent_warp": (prof["parent_ms"], prof["parent_launches"], kb["parent"])}
     dom = max(kernels, key=lambda k: kernels[k][0])
     k_ms, k_launches, k_bytes = kernels[dom]
     per_launch_bytes = k_bytes * prof_runs / max(k_launches, 1)
     avg_ms = k_ms / max(k_launches, 1)
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": ncu_traffic(dom),
+                "frac": achieved / peak if achieved else None, "traffic": ncu_traffic(dom, args.workload),
                 "kernel": dom, "peak_kind": f"{peak_kind} (copy bandwidth, burst)",
                 "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": per_launch_bytes,
                 "share_of_profiled_time": k_ms / max(prof["parent_ms"] + prof["child_ms"] + prof["other_ms"], 1e-9)}
     solve_bytes = kb["solve"]
     step_roofline = {"algorithmic_bytes": solve_bytes, "achieved_gbs": solve_bytes / (ms_per_step * 1e-3) / 1e9,
                      "frac": solve_bytes / (ms_per_step * 1e-3) / 1e9 / peak}
+    breakdown = {k: prof[k] for k in ("parent_ms", "child_ms", "other_ms", "parent_launches", "child_launches",
+                                      "longest_level_ms", "levels")}
+    breakdown["level_parents"] = prof.get("level_parents")
 
     # end to end through the C ABI from pinned host buffers
-    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
-    col_h = torch.from_numpy(g.col).pin_memory()
-    w_h = torch.from_numpy(g.w.view(np.int32)).pin_memory()
-    out_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
-    e2e_ms = []
-    for k in range(args.e2e_steps + 1):
-        flush.zero_()
-        torch.cuda.synchronize(dev)
-        t = time.perf_counter()
-        npb.np_sssp_host(ctx.handle, rp_h, col_h, w_h, 0, out_h, cfg, stream=stream)
-        dt = (time.perf_counter() - t) * 1e3
-        if k:
-            e2e_ms.append(dt)
-    e2e_ok = bool(np.array_equal(out_h.numpy().view(np.uint32), d_gpu))
-    e2e = {"value": mr / (statistics.median(e2e_ms) * 1e-3) / 1e9, "unit": "GTEPS",
-           "h2d_bytes_per_step": int(4 * (g.n + 1) + 8 * g.m), "d2h_bytes_per_step": int(4 * g.n),
-           "ms_per_step": statistics.median(e2e_ms), "matches_device_result": e2e_ok}
+    e2e_ms, h2d, d2h, e2e_res = W.e2e(cfg, args.e2e_steps, flush, dev)
+    e2e = {"value": units / (statistics.median(e2e_ms) * 1e-3) / 1e9, "unit": W.unit,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "ms_per_step": statistics.median(e2e_ms),
+           "matches_device_result": bool(np.array_equal(e2e_res, res_gpu))}
 
     # CPU baseline: the oracle as it stands, one core, bounded sample; also the parity check
     cpu = None
     parity = None
     if ws == 1 and not args.no_cpu:
-        import oracle
         ts = []
         ref = None
         t_end = time.perf_counter() + args.cpu_seconds
         while time.perf_counter() < t_end or not ts:
             t = time.perf_counter()
-            ref = oracle.sssp(g.row_ptr, g.col, g.w, 0)
+            ref = W.oracle()
             ts.append(time.perf_counter() - t)
-        parity = bool(np.array_equal(ref, d_gpu))
-        cpu = {"value": mr / statistics.mean(ts) / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-               "sample": f"{len(ts)} full Dijkstra solves of the workload ({sum(ts):.1f} s)",
+        parity = bool(np.array_equal(ref, res_gpu))
+        cpu = {"value": units / statistics.mean(ts) / 1e9, "unit": W.unit, "cores": 1, "kind": "oracle",
+               "sample": f"{len(ts)} full solves of the workload ({sum(ts):.1f} s)",
                "ms_per_solve": statistics.mean(ts) * 1e3}
 
-    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+    line = {"metric": metric, "value": value, "unit": W.unit, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": CONFIG,
+            "vs_baseline": None, "dtype": "f32" if wl["kind"] == "bezier" else "u32", "data": "synthetic",
+            "config": dict(wl["config"], l2=L2_NOTE),
             "form": "threshold 32 + coarsening 8 (32-thread child blocks) + grid aggregation (atomic scan), "
                     "while-graph level loop",
             "ms_per_solve": {"median": statistics.median(ms), "min": min(ms)},
-            "edges_reached": mr, "levels": st["levels"], "relaxations": st["items"],
+            "units_per_solve": units, "levels": st["levels"], "child_items": st["items"],
             "speedup_vs_plain_cdp": forms["plain_cdp"]["ms_per_solve"] / statistics.median(ms),
             "speedup_vs_nodp": forms["nodp"]["ms_per_solve"] / statistics.median(ms),
             "forms": forms, "roofline": roofline, "step_roofline": step_roofline,
             "cpu_baseline": cpu, "parity_vs_oracle": parity, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": gpu_launches, "profile_breakdown": prof}
+            "gpu_launches": gpu_launches, "profile_breakdown": breakdown}
     print(json.dumps(line), flush=True)
     ctx.close()
     if distributed:
@@ -391,6 +580,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sssp-rmat20")
     ap.add_argument("--cdp-steps", type=int, default=3, help="timed solves of the slow comparison forms")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

@@ -65,7 +65,9 @@ typedef int32_t np_status;
 
 /* ---- configuration (Sections III-V; the paper's _THRESHOLD/_CFACTOR macros
  *      and aggregation-granularity choice become runtime fields) ---- */
-#define NP_VARIANT_NODP 0     /* parents loop over their children; no launch code */
+#define NP_VARIANT_NODP 0     /* parents loop over their children; no launch code (warp-tiled parent
+                                 kernel; with NP_GRAN_NONE the CTA-tiled kernel of the device-launch
+                                 forms with its launch code compiled out, Section VII-D) */
 #define NP_VARIANT_CDP 1      /* dynamic parallelism with optional T, C and A */
 
 #define NP_GRAN_NONE 0        /* one child grid per launching parent */
@@ -280,6 +282,12 @@ typedef struct np_profile {
 np_status np_profile_enable(np_ctx *ctx, int32_t on);
 /* Accumulated times since the last reset; reset != 0 clears them. */
 np_status np_profile_read(np_ctx *ctx, np_profile *out, int32_t reset);
+
+/* Tessellation end to end: ctrl_host in, offsets_host[ncurves + 1] and
+ * points_host[cap][2] out. */
+np_status np_bezier_host(np_ctx *ctx, const float *ctrl_host, int32_t ncurves, int32_t *offsets_host,
+                         float *points_host, int64_t cap, const np_config *cfg, void *stream,
+                         np_stats *stats);
 
 const char *np_status_string(np_status s);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */

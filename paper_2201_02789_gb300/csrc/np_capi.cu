@@ -248,7 +248,9 @@ Plan make_plan(const BodyKernels& K, const np_config& cfg) {
   Plan p;
   const int cfi = cf_index(cfg.cfactor);
   if (cfg.variant == NP_VARIANT_NODP) {
-    p.parent = K.parent_nodp;
+    // warp tiles; with granularity NONE the CTA-tiled kernel of the
+    // device-launch forms without its launch code (dead-launch-code baseline)
+    p.parent = cfg.granularity == NP_GRAN_NONE ? K.parent_nodp_cta : K.parent_nodp;
     p.mode = M_NODP;
     p.gran = G_NODP;
   } else if (cfg.granularity == NP_GRAN_GRID_HOST) {
@@ -963,6 +965,34 @@ np_status np_profile_read(np_ctx* c, np_profile* out, int32_t reset) {
   *out = c->prof;
   if (reset) c->prof = np_profile{};
   return NP_OK;
+}
+
+np_status np_bezier_host(np_ctx* c, const float* ctrl_host, int32_t ncurves, int32_t* offsets_host,
+                         float* points_host, int64_t cap, const np_config* cfg, void* stream, np_stats* stats) {
+  if (!c || ncurves < 0 || (ncurves > 0 && !ctrl_host) || !offsets_host || cap < 0 || (cap > 0 && !points_host))
+    return NP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t b_ctrl = align_up(sizeof(float) * 6 * (size_t)ncurves), b_off = align_up(sizeof(int32_t) * ((size_t)ncurves + 1));
+  const size_t b_pts = align_up(sizeof(float) * 2 * (size_t)cap);
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    NP_CK(cudaSetDevice(c->device));
+    np_status st = stage_bytes(c, b_ctrl + b_off + b_pts + 256);
+    if (st != NP_OK) return st;
+  }
+  float* d_ctrl = reinterpret_cast<float*>(c->stage);
+  int32_t* d_off = reinterpret_cast<int32_t*>(c->stage + b_ctrl);
+  float* d_pts = reinterpret_cast<float*>(c->stage + b_ctrl + b_off);
+  if (ncurves) NP_CK(cudaMemcpyAsync(d_ctrl, ctrl_host, sizeof(float) * 6 * (size_t)ncurves, cudaMemcpyHostToDevice, s));
+  np_status st = np_bezier(c, d_ctrl, ncurves, d_off, d_pts, cap, cfg, stream, nullptr);
+  if (st != NP_OK) return st;
+  NP_CK(cudaMemcpyAsync(offsets_host, d_off, sizeof(int32_t) * ((size_t)ncurves + 1), cudaMemcpyDeviceToHost, s));
+  NP_CK(cudaStreamSynchronize(s));
+  const int64_t total = offsets_host[ncurves] < cap ? offsets_host[ncurves] : cap;
+  if (total > 0) NP_CK(cudaMemcpyAsync(points_host, d_pts, sizeof(float) * 2 * (size_t)total, cudaMemcpyDeviceToHost, s));
+  NP_CK(cudaStreamSynchronize(s));
+  np_stats tmp;
+  return np_sync(c, stream, stats ? stats : &tmp);
 }
 
 const char* np_status_string(np_status s) {

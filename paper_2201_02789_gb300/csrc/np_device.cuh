@@ -766,6 +766,10 @@ __device__ __forceinline__ void warp_stat(unsigned* s_stat, int k, unsigned v) {
 
 // The parent kernel of the device-launch forms (CTA tiles). GRAN selects the
 // launch scope; CF is the coarsening factor of the child kernel it launches.
+// GRAN == G_NODP compiles the same kernel with its launch code left out (every
+// parent serialises): set against the G_NONE kernel with a threshold above
+// every child count, the only difference is a launch site that never runs
+// (the dead-launch-code effect of Section VII-D).
 // Per tile: child counts, output offsets (Bezier), the launch decision, the
 // aggregation scan, records and launch; the serial children of the parents
 // below the threshold come last, so no scan ever waits behind a serial loop.
@@ -833,12 +837,12 @@ __global__ void NP_PARENT_BOUNDS parent_kernel(Args a) {
         N = 0;
       }
     }
-    const bool launch = valid && N >= T;
+    const bool launch = GRAN != G_NODP && valid && N >= T;
     const bool serial = valid && !launch && N > 0;
     warp_stat(s_stat, S_PARENTS, valid ? 1u : 0u);
     warp_stat(s_stat, S_ITEMS, (unsigned)N);
     warp_stat(s_stat, S_SERIAL, serial ? 1u : 0u);
-    {
+    if constexpr (GRAN != G_NODP) {
       warp_stat(s_stat, S_LAUNCHP, launch ? 1u : 0u);
       warp_stat(s_stat, S_CITEMS, launch ? (unsigned)N : 0u);
       const unsigned cg = launch ? (unsigned)ceil_div(ceil_div(N, CB), a.cfactor) : 0u;

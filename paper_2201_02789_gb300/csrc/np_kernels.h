@@ -18,6 +18,7 @@ inline int cf_index(int cf) {
 struct BodyKernels {
   const void* parent_nodp;                    // parent_warp<Body, 0>
   const void* parent_grid_host;               // parent_warp<Body, 1>
+  const void* parent_nodp_cta;                // parent_kernel<Body, G_NODP, 1>: CTA tiles, no launch code
   const void* parent[4][kNumCF];              // [NONE, WARP, BLOCK, MULTIBLOCK/GRID_DEVICE][cf]
   const void* child_direct[kNumCF];
   const void* child_agg[kNumCF];

@@ -19,6 +19,7 @@ inline BodyKernels make_table() {
   BodyKernels t{};
   t.parent_nodp = (const void*)parent_warp<Body, 0>;
   t.parent_grid_host = (const void*)parent_warp<Body, 1>;
+  t.parent_nodp_cta = (const void*)parent_kernel<Body, G_NODP, 1>;
   fill_parent_row<Body, G_NONE>(t.parent[0]);
   fill_parent_row<Body, G_WARP>(t.parent[1]);
   fill_parent_row<Body, G_BLOCK>(t.parent[2]);

@@ -128,6 +128,7 @@ _SIGS = {
     "np_sssp_host": [_VP, _I32, _I64, _VP, _VP, _VP, _I32, _VP, ctypes.POINTER(np_config), _VP,
                      ctypes.POINTER(np_stats)],
     "np_bezier_noalloc": [_VP, _I32, _VP, _VP, _I64, ctypes.POINTER(np_config), _VP],
+    "np_bezier_host": [_VP, _VP, _I32, _VP, _VP, _I64, ctypes.POINTER(np_config), _VP, ctypes.POINTER(np_stats)],
     "np_profile_enable": [_VP, _I32],
     "np_profile_read": [_VP, ctypes.POINTER(np_profile), _I32],
     "np_status_string": [_I32],
@@ -323,6 +324,15 @@ def np_profile_read(ctx, reset: bool = False) -> dict:
     p = np_profile()
     _check(lib().np_profile_read(ctx, ctypes.byref(p), 1 if reset else 0), "np_profile_read", True)
     return p.as_dict()
+
+
+def np_bezier_host(ctx, ctrl, ncurves: int, offsets_out, points_out, cap: int, cfg=None, stream=None,
+                   stats: bool = False, check: bool = True):
+    st, want = _stats_arg(stats)
+    s = lib().np_bezier_host(ctx, _ptr(ctrl), int(ncurves), _ptr(offsets_out), _ptr(points_out), int(cap),
+                             ctypes.byref(_cfg(cfg)), _stream(stream), ctypes.byref(st) if want else None)
+    _check(s, "np_bezier_host", check)
+    return (s, st.as_dict()) if want else s
 
 
 # ------------------------------------------------------------ configurations
