@@ -168,6 +168,131 @@ np_status np_bfs(np_ctx *ctx, const np_csr *g, int32_t src, int32_t *level,
 np_status np_sssp(np_ctx *ctx, const np_csr *g, int32_t src, uint32_t *dist,
                   const np_config *cfg, void *stream, np_stats *stats);
 
+/* ---- several traversals of one graph in one level loop ----
+ * nsrc queries from sources[q] (host array) on the same graph. Query q's
+ * vertices are ids q*ld + v, so the frontiers of all queries form one parent
+ * set per level and their children aggregate into the same child grids
+ * (Section V's aggregation, applied across queries). Row q of level / dist
+ * (device, nsrc*ld elements, row stride ld) receives query q's result as
+ * np_bfs / np_sssp define it; elements n..ld-1 of a row are left unreached.
+ * ld must be a power of two >= n with nsrc*ld < 2^31. The workspace scales
+ * with nsrc*ld (about 36 bytes per element). */
+np_status np_bfs_multi(np_ctx *ctx, const np_csr *g, int32_t nsrc, const int32_t *sources,
+                       int32_t *level, int64_t ld, const np_config *cfg, void *stream,
+                       np_stats *stats);
+np_status np_sssp_multi(np_ctx *ctx, const np_csr *g, int32_t nsrc, const int32_t *sources,
+                        uint32_t *dist, int64_t ld, const np_config *cfg, void *stream,
+                        np_stats *stats);
+
+/* ---- batched solves: many independent instances in one graph launch ----
+ * (The paper runs one instance at a time; batching applies its aggregation
+ * across instances.) np_batch_create copies `count` device CSR graphs
+ * (graphs[i] a host array of descriptors) into per-group disjoint unions:
+ * instances are grouped into size classes by floor(log2 n), `class_log2_width`
+ * powers of two per class, and a class is split into groups of at most
+ * `max_group_edges` edges. A group is solved as one multi-source traversal of
+ * its union graph (its components are disjoint, so every instance gets
+ * exactly its own result). np_batch_run launches one CUDA graph in which every
+ * group is a parallel branch: unreached fill, source seeding, and a
+ * conditional-while level loop. Only forms without device-side launches can
+ * sit in a conditional body: NP_VARIANT_NODP, or NP_VARIANT_CDP with
+ * NP_GRAN_GRID_HOST (others get NP_ERR_UNSUPPORTED). The batch owns its union
+ * copies (device memory about the inputs' size) and workspaces; the inputs
+ * may be freed after np_batch_create returns. */
+#define NP_BATCH_BFS 0
+#define NP_BATCH_SSSP 1
+typedef struct np_batch_options {
+  int32_t kind;               /* NP_BATCH_BFS or NP_BATCH_SSSP */
+  int32_t class_log2_width;   /* powers of two of n per size class (0 = 2) */
+  int64_t max_group_edges;    /* a group holds one instance, or several with at most
+                               * this many edges in total (0 = 2^30; < 2^31) */
+  np_config config;           /* initial configuration of every class */
+} np_batch_options;
+
+typedef struct np_batch_class {
+  int32_t log2_lo;            /* instances with floor(log2 n) in [log2_lo, log2_lo + width) */
+  int32_t instances;
+  int32_t groups;
+  int32_t reserved;
+  int64_t vertices;
+  int64_t edges;
+  np_config config;           /* configuration in use */
+  double tuned_ms;            /* the class's time under `config` when tuned (0 = not tuned) */
+  int32_t candidates;         /* configurations the tuner timed */
+  int32_t reserved2;
+} np_batch_class;
+
+typedef struct np_batch np_batch;
+
+/* sources: host [count], 0 <= sources[i] < graphs[i].n. SSSP needs weights. */
+np_status np_batch_create(np_ctx *ctx, int32_t count, const np_csr *graphs, const int32_t *sources,
+                          const np_batch_options *opt, np_batch **out);
+np_status np_batch_destroy(np_batch *b);
+/* Result layout: vertex v of instance i is out[offsets[i] + v]; total elements. */
+np_status np_batch_layout(const np_batch *b, int64_t *offsets, int64_t *total);
+np_status np_batch_classes(const np_batch *b, np_batch_class *out, int32_t max, int32_t *nclasses);
+np_status np_batch_set_config(np_batch *b, int32_t cls, const np_config *cfg);
+/* Autotuner. For each class, runs the class's groups alone under each
+ * candidate configuration (no dynamic parallelism; grid-host aggregation with
+ * threshold T in {8, 32, 128, 512}, coarsening factor in {2, 8} and child
+ * block in {32, 128}), `reps` times each (0 = 3), and keeps the configuration
+ * with the least minimum time. `out` (device, total elements) is overwritten. */
+np_status np_batch_tune(np_batch *b, void *out, int32_t reps, void *stream);
+/* Solves every instance into `out` (device int32 levels or uint32 distances,
+ * total elements). stats (nullable, waits) are summed over groups. */
+np_status np_batch_run(np_batch *b, void *out, void *stream, np_stats *stats);
+
+/* ---- serving: continuous batching of traversal queries ----
+ * (The paper has no serving layer.) A server keeps `ngraphs` device graphs
+ * resident (the caller keeps them alive) and one pool per (graph, kind).
+ * A pool holds S query slots: per-slot level or distance arrays of
+ * npad = next power of two >= n elements, and one level loop whose frontier
+ * holds the vertices (slot*npad + v) of every query in the pool, so the
+ * queries' children aggregate into the same grids. Memory-based admission:
+ * the budget is divided evenly over the pools and each pool gets
+ * S = min(max_slots, share / bytes_per_slot) slots (NP_ERR_NOMEM if a pool
+ * gets none). np_server_submit only queues a query. np_server_step, for
+ * every pool with work: admits queued queries into free slots (between
+ * levels: the slot is reset and its source joins the current frontier),
+ * runs `levels_per_step` levels, counts each slot's frontier entries and
+ * copies finished queries (no entries left) to their `out` arrays, all as
+ * one CUDA graph per pool on the pool's own stream, so pools overlap on the
+ * device; then it waits and marks finished queries done. Results equal
+ * np_bfs / np_sssp from the same source. */
+typedef struct np_server_options {
+  uint64_t memory_budget;     /* bytes for slot state (0 = a quarter of free device memory) */
+  int32_t max_slots;          /* per pool (0 = 64) */
+  int32_t levels_per_step;    /* 0 = 2 */
+  np_config bfs_config;       /* forms without device-side launches only */
+  np_config sssp_config;
+} np_server_options;
+
+typedef struct np_query_info {
+  int32_t done;               /* 1 once `out` holds the result */
+  int32_t graph;
+  int32_t kind;               /* NP_BATCH_BFS or NP_BATCH_SSSP */
+  int32_t slot;               /* -1 while queued */
+  int64_t submit_step;        /* server step counter at submission, admission, completion */
+  int64_t admit_step;
+  int64_t finish_step;
+} np_query_info;
+
+typedef struct np_server np_server;
+
+np_status np_server_create(np_ctx *ctx, const np_csr *graphs, int32_t ngraphs,
+                           const np_server_options *opt, np_server **out);
+np_status np_server_destroy(np_server *s);
+/* Slots and bytes per slot of pool (graph, kind). */
+np_status np_server_pool_info(const np_server *s, int32_t graph, int32_t kind, int32_t *slots,
+                              uint64_t *bytes_per_slot);
+/* Queues a query; out is a device array of graphs[graph].n int32 levels (BFS)
+ * or uint32 distances (SSSP), written when the query finishes. */
+np_status np_server_submit(np_server *s, int32_t graph, int32_t kind, int32_t src, void *out,
+                           int64_t *ticket);
+/* One serving round (see above). *in_flight = queries queued or resident after it. */
+np_status np_server_step(np_server *s, int32_t *in_flight);
+np_status np_server_poll(const np_server *s, int64_t ticket, np_query_info *info);
+
 /* Quadratic Bezier tessellation (Section VII, BT benchmark). ctrl is
  * float[ncurves][3][2]. Parent = curve c with curvature
  * kappa = |P0 - 2P1 + P2| / |P2 - P0| and N = clamp(ceil(sqrt(kappa)*64), 4, 4096)

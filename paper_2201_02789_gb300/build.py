@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libnestpar.so")
-SOURCES = ["np_capi.cu", "np_bfs.cu", "np_sssp.cu", "np_bezier.cu", "np_noalloc.cu"]
+SOURCES = ["np_capi.cu", "np_engine.cu", "np_batch.cu", "np_server.cu", "np_bfs.cu", "np_sssp.cu", "np_bezier.cu",
+           "np_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-rdc=true", "-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -82,3 +83,21 @@ def build(force: bool = False, verbose: bool = False, defines: tuple[str, ...] =
 
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+
+
+GEN_SRC = os.path.join(PKG, "gen_native.c")
+GEN_LIB = os.path.join(BUILD, "libnpgen.so")
+
+
+def build_gen(force: bool = False) -> str:
+    """Compile the C twin of the input generator (gen_native.c) with gcc."""
+    if not force and os.path.exists(GEN_LIB) and os.path.getmtime(GEN_LIB) >= os.path.getmtime(GEN_SRC):
+        return GEN_LIB
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = GEN_LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", GEN_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"gcc failed on gen_native.c:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, GEN_LIB)
+    return GEN_LIB

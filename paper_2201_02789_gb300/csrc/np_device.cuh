@@ -123,7 +123,10 @@ struct BodyArgs {
   int* next_count;
   LevelState* st;
   int L;                         // BFS writes L+1; SSSP stamps L+1
-  int pad;
+  // Several traversals of one graph at once: a vertex id is q * 2^k + v, the
+  // graph vertex is id & vmask and per-query state is indexed by the id; a
+  // single traversal has vmask = all ones.
+  int vmask;
 };
 
 struct Args {
@@ -473,16 +476,18 @@ struct BfsBody {
   static constexpr bool kPushes = true;
   struct P {
     int base;
+    int qbase;   // query part of the ids of this parent's children
   };
   struct F {
     int v;
   };
   __device__ static void count(const Args& a, int pid, int& base, int& N) {
-    base = __ldg(&a.row_ptr[pid]);
-    N = __ldg(&a.row_ptr[pid + 1]) - base;
+    const int u = pid & a.b.vmask;
+    base = __ldg(&a.row_ptr[u]);
+    N = __ldg(&a.row_ptr[u + 1]) - base;
   }
-  __device__ static P parent(const BodyArgs&, int, int base, int) { return P{base}; }
-  __device__ static F fetch(const BodyArgs& b, const P& p, int i) { return F{__ldg(&b.col[p.base + i])}; }
+  __device__ static P parent(const BodyArgs& b, int pid, int base, int) { return P{base, pid & ~b.vmask}; }
+  __device__ static F fetch(const BodyArgs& b, const P& p, int i) { return F{p.qbase | __ldg(&b.col[p.base + i])}; }
   template <int K>
   __device__ static void apply_batch(const BodyArgs& b, const P&, const int (&)[K], const F (&f)[K],
                                      const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
@@ -509,20 +514,22 @@ struct SsspBody {
   struct P {
     int base;
     unsigned du;
+    int qbase;   // query part of the ids of this parent's children
   };
   struct F {
     int v;
     unsigned w;
   };
   __device__ static void count(const Args& a, int pid, int& base, int& N) {
-    base = __ldg(&a.row_ptr[pid]);
-    N = __ldg(&a.row_ptr[pid + 1]) - base;
+    const int u = pid & a.b.vmask;
+    base = __ldg(&a.row_ptr[u]);
+    N = __ldg(&a.row_ptr[u + 1]) - base;
   }
   __device__ static P parent(const BodyArgs& b, int pid, int base, int) {
-    return P{base, __ldcg(&b.dist[pid])};
+    return P{base, __ldcg(&b.dist[pid]), pid & ~b.vmask};
   }
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) {
-    return F{__ldg(&b.col[p.base + i]), __ldg(&b.w[p.base + i])};
+    return F{p.qbase | __ldg(&b.col[p.base + i]), __ldg(&b.w[p.base + i])};
   }
   template <int K>
   __device__ static void apply_batch(const BodyArgs& b, const P& p, const int (&)[K], const F (&f)[K],

@@ -1,0 +1,600 @@
+// Host engine: workspaces, plans, grids and the level-loop drivers.
+//
+// Level loop. A level is one parent grid (persistent CTAs over the frontier,
+// which lives in device memory) plus, for grid-host aggregation, one
+// stream-ordered persistent child grid whose size is read from device memory.
+// Forms without a device launch site (NODP, grid-host aggregation) run the
+// whole loop inside a conditional-while CUDA graph: `unroll` levels per body
+// iteration, a one-thread kernel setting the condition, no host round trip.
+// Kernels containing device launches cannot sit in a conditional body, so the
+// device-launch forms replay a graph of `unroll` levels from the host and read
+// the frontier size back after each replay. NP_DRIVER_HOST is the paper's own
+// form: one host launch per level and a read-back after each.
+#include "np_engine.h"
+
+#include <climits>
+#include <cstring>
+
+namespace nestpar {
+
+np_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return NP_OK;
+  if (e == cudaErrorMemoryAllocation) return NP_ERR_NOMEM;
+  return NP_ERR_CUDA;
+}
+
+np_status status_from_bits(unsigned bits) {
+  if (bits & kErrTimeout) return NP_ERR_TIMEOUT;
+  if (bits & kErrCapacity) return NP_ERR_CAPACITY;
+  if (bits & kErrLaunch) return NP_ERR_LAUNCH;
+  return NP_OK;
+}
+
+// ------------------------------------------------------------- device side
+
+__device__ __forceinline__ void reset_slots(LevelState* st) {
+  for (int k = 0; k < 4; k++) {
+    st->ticket[k] = 0;
+    st->agg_records[k] = 0;
+    st->agg_blocks[k] = 0;
+    st->agg_acc[k] = 0ull;
+  }
+  for (int k = 0; k < S_N; k++) st->s[k] = 0ull;
+  st->body_iters = 0;
+  st->solve_id += 1;
+}
+
+__global__ void init_solve_kernel(LevelState* st, int kind, int n, int src, int* level, unsigned* dist,
+                                  int* stamp, int* fr0, int max_levels) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    if (kind == 0) {
+      level[v] = v == src ? 0 : -1;
+    } else {
+      dist[v] = v == src ? 0u : 0xffffffffu;
+      stamp[v] = -1;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    fr0[0] = src;
+    st->base = 0;
+    st->count[0] = 1;
+    st->count[1] = 0;
+    st->count[2] = 0;
+    st->max_levels = max_levels;
+    reset_slots(st);
+  }
+}
+
+__global__ void init_fixed_kernel(LevelState* st) { reset_slots(st); }
+
+__global__ void fill_unreached_kernel(int kind, long long total, int* level, unsigned* dist, int* stamp) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total; v += stride) {
+    if (kind == 0) {
+      level[v] = -1;
+    } else {
+      dist[v] = 0xffffffffu;
+      stamp[v] = -1;
+    }
+  }
+}
+
+__global__ void seed_sources_kernel(LevelState* st, int kind, const int* ids, int nsrc, int* level, unsigned* dist,
+                                    int* fr0, int max_levels) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsrc; i += gridDim.x * blockDim.x) {
+    const int id = ids[i];
+    if (kind == 0)
+      level[id] = 0;
+    else
+      dist[id] = 0u;
+    fr0[i] = id;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->base = 0;
+    st->count[0] = nsrc;
+    st->count[1] = 0;
+    st->count[2] = 0;
+    st->max_levels = max_levels;
+    reset_slots(st);
+  }
+}
+
+// Between graph bodies or chunks: the next body position 0 is level base + K.
+__global__ void advance_base_kernel(LevelState* st, int K) { st->base += K; }
+
+// End of a conditional-while body of K levels: move base on and continue while
+// the next level has parents. The iteration cap turns a level loop that failed
+// to terminate into an error instead of an endless loop.
+__global__ void set_cond_kernel(LevelState* st, cudaGraphConditionalHandle h, int K) {
+  const int L = st->base + K;
+  st->base = L;
+  const int c = st->count[L % 3];
+  const int it = ++st->body_iters;
+  bool more = c > 0 && L < st->max_levels;
+  if (more && it > st->max_levels + 16) {
+    st->error |= kErrTimeout;
+    more = false;
+  }
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// --------------------------------------------------------------- host side
+
+Layout layout_for(int64_t parents) {
+  Layout L{};
+  L.P2 = ((parents + 1023) / 1024) * 1024 + 1024;
+  L.T = L.P2 / 32 + 64;
+  const int64_t fr = L.P2;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = align_up(o + bytes);
+    return r;
+  };
+  L.off_fr0 = take(sizeof(int) * fr);
+  L.off_fr1 = take(sizeof(int) * fr);
+  L.off_stamp = take(sizeof(int) * L.P2);
+  L.off_rec = take(sizeof(int4) * L.P2);
+  L.off_boff = take(sizeof(int) * L.P2);
+  L.off_lb_flag = take(sizeof(unsigned long long) * L.T);
+  L.off_lb_agg = take(sizeof(uint4) * L.T);
+  L.off_lb_incl = take(sizeof(uint4) * L.T);
+  L.off_ob_flag = take(sizeof(unsigned long long) * L.T);
+  L.off_ob_agg = take(sizeof(uint4) * L.T);
+  L.off_ob_incl = take(sizeof(uint4) * L.T);
+  L.off_grp_ctr = take(sizeof(int) * L.T);
+  L.off_grp_acc = take(sizeof(unsigned long long) * L.T);
+  L.off_grp_total = take(sizeof(uint2) * L.T);
+  L.total = o;
+  return L;
+}
+
+np_status engine_init(Engine& e, int device) {
+  e.device = device;
+  cudaDeviceProp prop;
+  NP_CK(cudaGetDeviceProperties(&prop, device));
+  e.sms = prop.multiProcessorCount;
+  NP_CK(cudaMallocHost(&e.pin, 64));
+  NP_CK(cudaMallocHost(&e.pin_state, sizeof(LevelState)));
+  NP_CK(cudaStreamCreateWithFlags(&e.cap_stream, cudaStreamNonBlocking));
+  for (int k = 0; k < 4; k++) NP_CK(cudaEventCreate(&e.ev[k]));
+  return NP_OK;
+}
+
+void engine_release(Engine& e) {
+  if (e.pin) cudaFreeHost(e.pin);
+  if (e.pin_state) cudaFreeHost(e.pin_state);
+  if (e.cap_stream) cudaStreamDestroy(e.cap_stream);
+  for (int k = 0; k < 4; k++)
+    if (e.ev[k]) cudaEventDestroy(e.ev[k]);
+  e = Engine{};
+}
+
+np_status ws_init(Workspace& w) {
+  NP_CK(cudaMalloc(&w.st, sizeof(LevelState)));
+  NP_CK(cudaMemset(w.st, 0, sizeof(LevelState)));
+  return NP_OK;
+}
+
+void ws_drop_graphs(Workspace& w) {
+  for (auto& kv : w.graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  w.graphs.clear();
+}
+
+void ws_release(Workspace& w) {
+  ws_drop_graphs(w);
+  if (w.ws) cudaFree(w.ws);
+  if (w.st) cudaFree(w.st);
+  w.ws = nullptr;
+  w.st = nullptr;
+  w.cap_parents = 0;
+}
+
+np_status ws_ensure(Workspace& w, int64_t parents) {
+  if (parents <= w.cap_parents && w.ws) return NP_OK;
+  int64_t want = parents < 4096 ? 4096 : parents;
+  Layout L = layout_for(want);
+  ws_drop_graphs(w);
+  if (w.ws) {
+    NP_CK(cudaDeviceSynchronize());
+    cudaFree(w.ws);
+    w.ws = nullptr;
+    w.cap_parents = 0;
+  }
+  unsigned char* p = nullptr;
+  NP_CK(cudaMalloc(&p, L.total));
+  NP_CK(cudaMemset(p, 0, L.total));
+  w.ws = p;
+  w.lay = L;
+  w.cap_parents = want;
+  return NP_OK;
+}
+
+int occupancy(Engine& e, const void* fn, int block) {
+  auto key = std::make_pair(fn, block);
+  auto it = e.occ.find(key);
+  if (it != e.occ.end()) return it->second;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, 0) != cudaSuccess || n < 1) n = 1;
+  e.occ[key] = n;
+  return n;
+}
+
+np_status check_config(const np_config* cfg) {
+  if (!cfg) return NP_ERR_INVALID;
+  if (cfg->variant != NP_VARIANT_NODP && cfg->variant != NP_VARIANT_CDP) return NP_ERR_INVALID;
+  if (cf_index(cfg->cfactor) < 0) return NP_ERR_INVALID;
+  if (cfg->granularity < NP_GRAN_NONE || cfg->granularity > NP_GRAN_GRID_HOST) return NP_ERR_INVALID;
+  if (cfg->granularity == NP_GRAN_MULTIBLOCK && cfg->group_blocks < 1) return NP_ERR_INVALID;
+  if (cfg->agg_threshold < 0) return NP_ERR_INVALID;
+  if (cfg->child_block < 32 || cfg->child_block > 1024 || cfg->child_block % 32) return NP_ERR_INVALID;
+  if (cfg->parent_block < 64 || cfg->parent_block > kMaxParentBlock || cfg->parent_block % 32) return NP_ERR_INVALID;
+  if (cfg->scan != NP_SCAN_LOOKBACK && cfg->scan != NP_SCAN_ATOMIC) return NP_ERR_INVALID;
+  if (cfg->driver < NP_DRIVER_AUTO || cfg->driver > NP_DRIVER_WHILE) return NP_ERR_INVALID;
+  if (cfg->unroll < 1 || cfg->unroll > 16) return NP_ERR_INVALID;
+  if (cfg->parent_grid < 0) return NP_ERR_INVALID;
+  for (int k = 0; k < 4; k++)
+    if (cfg->reserved[k] != 0) return NP_ERR_INVALID;
+  return NP_OK;
+}
+
+Plan make_plan(const BodyKernels& K, const np_config& cfg) {
+  Plan p;
+  const int cfi = cf_index(cfg.cfactor);
+  if (cfg.variant == NP_VARIANT_NODP) {
+    // warp tiles; with granularity NONE the CTA-tiled kernel of the
+    // device-launch forms without its launch code (dead-launch-code baseline)
+    p.parent = cfg.granularity == NP_GRAN_NONE ? K.parent_nodp_cta : K.parent_nodp;
+    p.mode = M_NODP;
+    p.gran = G_NODP;
+  } else if (cfg.granularity == NP_GRAN_GRID_HOST) {
+    p.parent = K.parent_grid_host;
+    p.child = K.child_agg[cfi];
+    p.mode = M_GRID_HOST;
+    p.gran = G_GRID_HOST;
+  } else {
+    int row = 0;
+    switch (cfg.granularity) {
+      case NP_GRAN_NONE: row = 0; break;
+      case NP_GRAN_WARP: row = 1; break;
+      case NP_GRAN_BLOCK: row = 2; break;
+      default: row = 3; break;  // multi-block and grid-device share one kernel
+    }
+    p.parent = K.parent[row][cfi];
+    p.mode = M_DEVICE_LAUNCH;
+    p.gran = cfg.granularity;
+  }
+  return p;
+}
+
+void base_args(const Workspace& w, const np_config& cfg, Args& a) {
+  std::memset(&a, 0, sizeof(a));
+  a.st = w.st;
+  a.fr0 = wsp<int>(w, w.lay.off_fr0);
+  a.fr1 = wsp<int>(w, w.lay.off_fr1);
+  a.rec = wsp<int4>(w, w.lay.off_rec);
+  a.boff = wsp<int>(w, w.lay.off_boff);
+  a.lb_flag = wsp<unsigned long long>(w, w.lay.off_lb_flag);
+  a.lb_agg = wsp<uint4>(w, w.lay.off_lb_agg);
+  a.lb_incl = wsp<uint4>(w, w.lay.off_lb_incl);
+  a.ob_flag = wsp<unsigned long long>(w, w.lay.off_ob_flag);
+  a.ob_agg = wsp<uint4>(w, w.lay.off_ob_agg);
+  a.ob_incl = wsp<uint4>(w, w.lay.off_ob_incl);
+  a.grp_ctr = wsp<int>(w, w.lay.off_grp_ctr);
+  a.grp_acc = wsp<unsigned long long>(w, w.lay.off_grp_acc);
+  a.grp_total = wsp<uint2>(w, w.lay.off_grp_total);
+  a.threshold = cfg.threshold;
+  a.cfactor = cfg.cfactor;
+  a.child_block = cfg.child_block;
+  a.group_blocks = cfg.granularity == NP_GRAN_MULTIBLOCK ? cfg.group_blocks : 0;
+  a.agg_threshold = (cfg.granularity == NP_GRAN_WARP || cfg.granularity == NP_GRAN_BLOCK) ? cfg.agg_threshold : 0;
+  a.scan = cfg.scan;
+  a.b.st = w.st;
+  a.b.vmask = 0x7fffffff;
+  a.count_fixed = -1;
+}
+
+Grids grids_for(Engine& e, const Plan& p, const np_config& cfg, int64_t max_parents) {
+  Grids g{};
+  g.pblock = cfg.parent_block;
+  g.cblock = cfg.child_block;
+  int64_t tiles = (max_parents + g.pblock - 1) / g.pblock;
+  if (tiles < 1) tiles = 1;
+  int64_t pg = cfg.parent_grid > 0 ? cfg.parent_grid : (int64_t)occupancy(e, p.parent, g.pblock) * e.sms;
+  if (pg > tiles) pg = tiles;
+  g.pgrid = (int)pg;
+  // the persistent child grid hosts cb-thread child blocks in CTAs of at least 256 threads
+  g.cthreads = g.cblock < 256 ? 256 : g.cblock;
+  g.cgrid = p.child ? occupancy(e, p.child, g.cthreads) * e.sms : 0;
+  return g;
+}
+
+int resolve_driver(const Plan& p, const np_config& cfg) {
+  if (cfg.driver != NP_DRIVER_AUTO) return cfg.driver;
+  return p.mode == M_DEVICE_LAUNCH ? NP_DRIVER_CHUNK : NP_DRIVER_WHILE;
+}
+
+namespace {
+
+AggSeg make_seg(const Args& a, const Grids& g, bool level_mode) {
+  AggSeg seg{};
+  seg.rec = a.rec;
+  seg.boff = a.boff;
+  seg.mode = a.scan == 0 ? 1 : 2;
+  seg.k = a.k;
+  seg.level_mode = level_mode ? 1 : 0;
+  seg.fr0 = a.fr0;
+  seg.fr1 = a.fr1;
+  seg.cb = g.cblock;
+  return seg;
+}
+
+BodyArgs child_body(const Args& a, bool level_mode) {
+  BodyArgs b = a.b;
+  if (!level_mode) {
+    b.L = a.L_fixed;
+    b.next = a.next_ovr;
+    b.next_count = a.next_count_ovr;
+  }
+  return b;
+}
+
+}  // namespace
+
+// Enqueues the grids of one level (level mode, at body position k) or of one
+// fixed pass.
+np_status enqueue_pass(const Plan& p, Args a, const Grids& g, bool level_mode, int k, cudaStream_t s) {
+  a.k = level_mode ? k : 0;
+  void* pargs[] = {&a};
+  NP_CK(cudaLaunchKernel(p.parent, dim3(g.pgrid), dim3(g.pblock), pargs, 0, s));
+  if (p.mode == M_GRID_HOST) {
+    AggSeg seg = make_seg(a, g, level_mode);
+    BodyArgs b = child_body(a, level_mode);
+    void* cargs[] = {&b, &seg};
+    NP_CK(cudaLaunchKernel(p.child, dim3(g.cgrid), dim3(g.cthreads), cargs, 0, s));
+  }
+  return NP_OK;
+}
+
+np_status enqueue_advance(LevelState* st, int K, cudaStream_t s) {
+  advance_base_kernel<<<1, 1, 0, s>>>(st, K);
+  NP_CK(cudaGetLastError());
+  return NP_OK;
+}
+
+// Profile mode: the grids of one level (or pass) launched one by one between
+// CUDA events, then waited for; times go to the engine's breakdown.
+np_status profiled_pass(Engine& e, const Workspace& w, const Plan& p, Args a, const Grids& g, bool level_mode,
+                        cudaStream_t s) {
+  a.k = 0;
+  void* pargs[] = {&a};
+  NP_CK(cudaEventRecord(e.ev[0], s));
+  NP_CK(cudaLaunchKernel(p.parent, dim3(g.pgrid), dim3(g.pblock), pargs, 0, s));
+  NP_CK(cudaEventRecord(e.ev[1], s));
+  bool child = false, other = false;
+  if (p.mode == M_GRID_HOST) {
+    AggSeg seg = make_seg(a, g, level_mode);
+    BodyArgs b = child_body(a, level_mode);
+    void* cargs[] = {&b, &seg};
+    NP_CK(cudaLaunchKernel(p.child, dim3(g.cgrid), dim3(g.cthreads), cargs, 0, s));
+    child = true;
+  }
+  NP_CK(cudaEventRecord(e.ev[2], s));
+  if (level_mode) {
+    advance_base_kernel<<<1, 1, 0, s>>>(w.st, 1);
+    NP_CK(cudaGetLastError());
+    other = true;
+  }
+  NP_CK(cudaEventRecord(e.ev[3], s));
+  NP_CK(cudaEventSynchronize(e.ev[3]));
+  float t01 = 0.f, t12 = 0.f, t23 = 0.f;
+  NP_CK(cudaEventElapsedTime(&t01, e.ev[0], e.ev[1]));
+  NP_CK(cudaEventElapsedTime(&t12, e.ev[1], e.ev[2]));
+  NP_CK(cudaEventElapsedTime(&t23, e.ev[2], e.ev[3]));
+  e.prof.parent_ms += t01;
+  e.prof.parent_launches += 1;
+  if (child) {
+    e.prof.child_ms += t12;
+    e.prof.child_launches += 1;
+  }
+  if (other) {
+    e.prof.other_ms += t23;
+    e.prof.other_launches += 1;
+  }
+  if (level_mode) {
+    const int k = e.prof.levels;
+    const double lvl = (double)t01 + (child ? (double)t12 : 0.0);
+    if (lvl > e.prof.longest_level_ms) e.prof.longest_level_ms = lvl;
+    if (k < NP_PROFILE_LEVELS) {
+      e.prof.level_parents[k] = e.prof_next_parents;
+      e.prof.level_parent_ms[k] = t01;
+      e.prof.level_child_ms[k] = child ? t12 : 0.0;
+      e.prof.levels = k + 1;
+    }
+  }
+  return NP_OK;
+}
+
+std::string graph_key(const char* tag, const Plan& p, const Args& a, const Grids& g, int unroll) {
+  std::string k(tag);
+  k.append(reinterpret_cast<const char*>(&p), sizeof(p));
+  k.append(reinterpret_cast<const char*>(&a), sizeof(a));
+  k.append(reinterpret_cast<const char*>(&g), sizeof(g));
+  k.append(reinterpret_cast<const char*>(&unroll), sizeof(unroll));
+  return k;
+}
+
+np_status cache_graph(Workspace& w, const std::string& key, cudaGraph_t graph, cudaGraphExec_t* out) {
+  cudaGraphExec_t exec = nullptr;
+  np_status st = instantiate(graph, &exec);
+  if (st != NP_OK) {
+    cudaGraphDestroy(graph);
+    return st;
+  }
+  if (w.graphs.size() >= 64) ws_drop_graphs(w);
+  w.graphs[key] = GraphEntry{graph, exec};
+  *out = exec;
+  return NP_OK;
+}
+
+np_status instantiate(cudaGraph_t graph, cudaGraphExec_t* exec) {
+  cudaError_t e = cudaGraphInstantiate(exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *exec = nullptr;
+    return e == cudaErrorInvalidValue ? NP_ERR_UNSUPPORTED : from_cuda(e);
+  }
+  return NP_OK;
+}
+
+np_status chunk_graph(Engine& e, Workspace& w, const Plan& p, const Args& a, const Grids& g, int K,
+                      cudaGraphExec_t* out) {
+  std::string key = graph_key("chunk", p, a, g, K);
+  auto it = w.graphs.find(key);
+  if (it != w.graphs.end()) {
+    *out = it->second.exec;
+    return NP_OK;
+  }
+  NP_CK(cudaStreamBeginCapture(e.cap_stream, cudaStreamCaptureModeThreadLocal));
+  np_status st = NP_OK;
+  for (int k = 0; k < K && st == NP_OK; k++) st = enqueue_pass(p, a, g, true, k, e.cap_stream);
+  if (st == NP_OK) st = enqueue_advance(w.st, K, e.cap_stream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(e.cap_stream, &graph);
+  if (st != NP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  NP_CK(ce);
+  return cache_graph(w, key, graph, out);
+}
+
+np_status add_while_node(Engine& e, LevelState* st, cudaGraph_t graph, const cudaGraphNode_t* deps, size_t ndeps,
+                         const Plan& p, const Args& a, const Grids& g, int K, cudaGraphNode_t* node) {
+  cudaGraphConditionalHandle h;
+  NP_CK(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  NP_CK(cudaGraphAddNode(node, graph, deps, nullptr, ndeps, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  NP_CK(cudaStreamBeginCaptureToGraph(e.cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  np_status s = NP_OK;
+  for (int k = 0; k < K && s == NP_OK; k++) s = enqueue_pass(p, a, g, true, k, e.cap_stream);
+  set_cond_kernel<<<1, 1, 0, e.cap_stream>>>(st, h, K);
+  cudaError_t le = cudaGetLastError();
+  cudaError_t ce = cudaStreamEndCapture(e.cap_stream, &body);
+  if (s != NP_OK) return s;
+  NP_CK(le);
+  NP_CK(ce);
+  return NP_OK;
+}
+
+np_status while_graph(Engine& e, Workspace& w, const Plan& p, const Args& a, const Grids& g, int K,
+                      cudaGraphExec_t* out) {
+  std::string key = graph_key("while", p, a, g, K);
+  auto it = w.graphs.find(key);
+  if (it != w.graphs.end()) {
+    *out = it->second.exec;
+    return NP_OK;
+  }
+  cudaGraph_t graph = nullptr;
+  NP_CK(cudaGraphCreate(&graph, 0));
+  cudaGraphNode_t node;
+  np_status st = add_while_node(e, w.st, graph, nullptr, 0, p, a, g, K, &node);
+  if (st != NP_OK) {
+    cudaGraphDestroy(graph);
+    return st;
+  }
+  return cache_graph(w, key, graph, out);
+}
+
+np_status read_header(Engine& e, const Workspace& w, cudaStream_t s, int* level, int* count) {
+  NP_CK(cudaMemcpyAsync(e.pin, w.st, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));   // base, count[3]
+  NP_CK(cudaStreamSynchronize(s));
+  *level = e.pin[0];
+  *count = e.pin[1 + e.pin[0] % 3];
+  return NP_OK;
+}
+
+np_status finish(Engine& e, const Workspace& w, cudaStream_t s, np_stats* stats) {
+  if (!stats) return NP_OK;
+  NP_CK(cudaMemcpyAsync(e.pin_state, w.st, sizeof(LevelState), cudaMemcpyDeviceToHost, s));
+  NP_CK(cudaStreamSynchronize(s));
+  const LevelState& h = *e.pin_state;
+  std::memset(stats, 0, sizeof(*stats));
+  stats->levels = h.s[S_LEVELS];
+  stats->parents = h.s[S_PARENTS];
+  stats->serial_parents = h.s[S_SERIAL];
+  stats->launch_parents = h.s[S_LAUNCHP];
+  stats->device_launches = h.s[S_DEVLAUNCH];
+  stats->aggregated_grids = h.s[S_AGGGRID];
+  stats->child_blocks = h.s[S_CBLOCKS];
+  stats->items = h.s[S_ITEMS];
+  stats->pushes = h.s[S_PUSHES];
+  stats->launch_failures = h.s[S_LFAIL];
+  stats->timeouts = h.s[S_TIMEOUT];
+  stats->child_items = h.s[S_CITEMS];
+  stats->graph_iterations = (uint64_t)h.body_iters;
+  stats->error = h.error;
+  if (h.error) {
+    NP_CK(cudaMemsetAsync(&w.st->error, 0, sizeof(unsigned), s));
+    NP_CK(cudaStreamSynchronize(s));
+  }
+  return status_from_bits(h.error);
+}
+
+np_status run_levels(Engine& e, Workspace& w, const Plan& p, const Args& a, const np_config& cfg, int64_t parents,
+                     int max_levels, cudaStream_t s) {
+  Grids g = grids_for(e, p, cfg, parents);
+  const int driver = resolve_driver(p, cfg);
+  if (driver == NP_DRIVER_WHILE && p.mode == M_DEVICE_LAUNCH) return NP_ERR_UNSUPPORTED;
+  if (e.profile) {
+    // per-level records describe this call only
+    e.prof.levels = 0;
+    e.prof.longest_level_ms = 0.0;
+    for (int iter = 0;; iter++) {
+      if (iter > max_levels + 16) return NP_ERR_TIMEOUT;
+      NP_TRY(profiled_pass(e, w, p, a, g, true, s));
+      int level = 0, count = 0;
+      NP_TRY(read_header(e, w, s, &level, &count));
+      e.prof_next_parents = count;
+      if (count <= 0 || level >= max_levels) break;
+    }
+    return NP_OK;
+  }
+  if (driver == NP_DRIVER_WHILE) {
+    cudaGraphExec_t exec;
+    NP_TRY(while_graph(e, w, p, a, g, cfg.unroll, &exec));
+    NP_CK(cudaGraphLaunch(exec, s));
+    return NP_OK;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (driver == NP_DRIVER_CHUNK) NP_TRY(chunk_graph(e, w, p, a, g, cfg.unroll, &exec));
+  for (int iter = 0;; iter++) {
+    if (iter > max_levels + 16) return NP_ERR_TIMEOUT;   // a level failed to advance
+    if (exec) {
+      NP_CK(cudaGraphLaunch(exec, s));
+    } else {
+      NP_TRY(enqueue_pass(p, a, g, true, 0, s));
+      NP_TRY(enqueue_advance(w.st, 1, s));
+    }
+    int level = 0, count = 0;
+    NP_TRY(read_header(e, w, s, &level, &count));
+    if (count <= 0 || level >= max_levels) break;
+  }
+  return NP_OK;
+}
+
+np_status check_csr(const np_csr* g, bool need_w) {
+  if (!g || !g->row_ptr || (!g->col_idx && g->m > 0) || g->n < 1 || g->m < 0 || g->m >= INT_MAX) return NP_ERR_INVALID;
+  if (need_w && !g->weights && g->m > 0) return NP_ERR_INVALID;
+  return NP_OK;
+}
+
+}  // namespace nestpar

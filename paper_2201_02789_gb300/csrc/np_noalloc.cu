@@ -133,6 +133,7 @@ extern "C" np_status np_bezier_noalloc(const float* ctrl, int32_t ncurves, int32
   a.offsets = offsets;
   a.cap = cap;
   a.b.st = state;
+  a.b.vmask = 0x7fffffff;
   a.b.ctrl = ctrl;
   a.b.points = reinterpret_cast<float2*>(points);
 

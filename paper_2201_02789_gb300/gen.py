@@ -30,7 +30,9 @@ Workload recipes (the paper's datasets are not available; these stand in):
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -161,9 +163,7 @@ def _rmat_edges(scale: int, count: int, first: int, seed: int, stream: int,
     Level ``l`` of edge ``e`` uses 16-bit field ``l % 4`` (least significant first) of
     output ``e * ceil(scale/4) + l // 4`` of the stream.
     """
-    ta = round(a * (1 << _RMAT_Q))
-    tb = ta + round(b * (1 << _RMAT_Q))
-    tc = tb + round(c * (1 << _RMAT_Q))
+    ta, tb, tc = _rmat_thresholds(a, b, c)
     words = (scale + 3) // 4                       # four 16-bit draws per 64-bit output
     raw = u64(seed, stream, first * words, count * words)
     # 16-bit fields in significance order, independent of host byte order
@@ -178,14 +178,63 @@ def _rmat_edges(scale: int, count: int, first: int, seed: int, stream: int,
     return src.astype(np.int64), dst.astype(np.int64)
 
 
+_NATIVE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libnpgen.so")
+_native_lib = None
+
+
+def native_available() -> bool:
+    """True when the C twin of the R-MAT recipe (gen_native.c) has been built."""
+    global _native_lib
+    if _native_lib is None and os.path.exists(_NATIVE_PATH):
+        L = ctypes.CDLL(_NATIVE_PATH)
+        L.npgen_rmat.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                 ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                 ctypes.c_uint32]
+        L.npgen_rmat.restype = ctypes.c_int
+        _native_lib = L
+    return _native_lib is not None
+
+
+def _rmat_thresholds(a: float, b: float, c: float) -> tuple[int, int, int]:
+    ta = round(a * (1 << _RMAT_Q))
+    tb = ta + round(b * (1 << _RMAT_Q))
+    tc = tb + round(c * (1 << _RMAT_Q))
+    return ta, tb, tc
+
+
+def rmat_native(scale: int, nv: int, me: int, a: float, b: float, c: float, seed: int,
+                weights: tuple[int, int] | None) -> Csr:
+    """gen.rmat through the C twin (same bytes; releases the GIL, so instances can be drawn in threads)."""
+    if not native_available():
+        raise RuntimeError("libnpgen.so is not built (paper_2201_02789_gb300.build.build_gen())")
+    ta, tb, tc = _rmat_thresholds(a, b, c)
+    row_ptr = np.empty(nv + 1, dtype=np.int32)
+    col = np.empty(max(me, 1), dtype=np.int32)
+    w = np.empty(max(me, 1), dtype=np.uint32) if weights is not None else None
+    rc = _native_lib.npgen_rmat(scale, nv, me, seed & ((1 << 64) - 1), S_RMAT, S_WEIGHT, ta, tb, tc,
+                                row_ptr.ctypes.data, col.ctypes.data, w.ctypes.data if w is not None else None,
+                                weights[0] if weights else 0, weights[1] if weights else 0)
+    if rc != 0:
+        raise RuntimeError("native R-MAT generation failed")
+    g = Csr(nv, row_ptr, col[:me])
+    if w is not None:
+        g.w = w[:me]
+    return g
+
+
 def rmat(scale: int = 20, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
          seed: int = 2, n: int | None = None, m: int | None = None,
-         weights: tuple[int, int] | None = (1, 255), chunk: int = 1 << 21) -> Csr:
-    """R-MAT digraph. Self-loops (and endpoints >= n when n < 2^scale) are redrawn."""
+         weights: tuple[int, int] | None = (1, 255), chunk: int = 1 << 21, native: bool | None = None) -> Csr:
+    """R-MAT digraph. Self-loops (and endpoints >= n when n < 2^scale) are redrawn.
+
+    ``native`` None uses the C twin when it is built (identical output), True requires it, False forbids it."""
     nv = (1 << scale) if n is None else n
     if nv > (1 << scale):
         raise ValueError("n exceeds 2^scale")
     me = edge_factor * nv if m is None else m
+    if native or (native is None and native_available()):
+        return rmat_native(scale, nv, me, a, b, c, seed, weights)
     src = np.empty(me, dtype=np.int64)
     dst = np.empty(me, dtype=np.int64)
     for lo in range(0, me, chunk):
@@ -262,6 +311,22 @@ def batch_specs(count: int = 512, seed: int = 4, log2_lo: float = 10.0, log2_hi:
         scale = max(1, math.ceil(math.log2(n)))
         out.append(BatchInstance(scale, n, int(efs[i]), seed * 1000003 + i))
     return out
+
+
+def batch_instance(spec: BatchInstance, weights: tuple[int, int] | None = (1, 255),
+                   native: bool | None = None) -> Csr:
+    """One batched-workload graph: R-MAT at scale ceil(log2 n) on n vertices, m = edge_factor * n."""
+    return rmat(spec.scale, spec.edge_factor, seed=spec.seed, n=spec.n, weights=weights, native=native)
+
+
+def batch_graphs(specs: list[BatchInstance], weights: tuple[int, int] | None = (1, 255),
+                 threads: int | None = None) -> list[Csr]:
+    """All instances of a batch, drawn in parallel threads by the C twin when it is built."""
+    if not native_available():
+        return [batch_instance(s, weights, native=False) for s in specs]
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 4) as ex:
+        return list(ex.map(lambda s: batch_instance(s, weights, native=True), specs))
 
 
 def random_sources(g: Csr, count: int, seed: int) -> np.ndarray:

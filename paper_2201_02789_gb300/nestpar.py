@@ -26,6 +26,7 @@ NP_SCAN_LOOKBACK, NP_SCAN_ATOMIC = 0, 1
 NP_DRIVER_AUTO, NP_DRIVER_HOST, NP_DRIVER_CHUNK, NP_DRIVER_WHILE = range(4)
 NP_COUNT_CSR_DEGREE, NP_COUNT_BEZIER = 0, 1
 NP_BODY_BFS_VISIT, NP_BODY_SSSP_RELAX, NP_BODY_BEZIER_EVAL = 0, 1, 2
+NP_BATCH_BFS, NP_BATCH_SSSP = 0, 1
 INT32_MAX = 2 ** 31 - 1
 
 GRAN_NAMES = {"none": NP_GRAN_NONE, "warp": NP_GRAN_WARP, "block": NP_GRAN_BLOCK,
@@ -109,6 +110,37 @@ class np_body(ctypes.Structure):
                 ("cap", ctypes.c_int64)]
 
 
+class np_batch_options(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("class_log2_width", ctypes.c_int32), ("max_group_edges", ctypes.c_int64),
+                ("config", np_config)]
+
+
+class np_batch_class(ctypes.Structure):
+    _fields_ = [("log2_lo", ctypes.c_int32), ("instances", ctypes.c_int32), ("groups", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("vertices", ctypes.c_int64), ("edges", ctypes.c_int64),
+                ("config", np_config), ("tuned_ms", ctypes.c_double), ("candidates", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved") and k != "config"}
+        d["config"] = self.config.as_dict()
+        return d
+
+
+class np_server_options(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
+                ("levels_per_step", ctypes.c_int32), ("bfs_config", np_config), ("sssp_config", np_config)]
+
+
+class np_query_info(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("graph", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("slot", ctypes.c_int32), ("submit_step", ctypes.c_int64), ("admit_step", ctypes.c_int64),
+                ("finish_step", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lock = threading.Lock()
 _lib = None
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
@@ -131,6 +163,23 @@ _SIGS = {
     "np_bezier_host": [_VP, _VP, _I32, _VP, _VP, _I64, ctypes.POINTER(np_config), _VP, ctypes.POINTER(np_stats)],
     "np_profile_enable": [_VP, _I32],
     "np_profile_read": [_VP, ctypes.POINTER(np_profile), _I32],
+    "np_bfs_multi": [_VP, ctypes.POINTER(np_csr), _I32, _VP, _VP, _I64, ctypes.POINTER(np_config), _VP,
+                     ctypes.POINTER(np_stats)],
+    "np_sssp_multi": [_VP, ctypes.POINTER(np_csr), _I32, _VP, _VP, _I64, ctypes.POINTER(np_config), _VP,
+                      ctypes.POINTER(np_stats)],
+    "np_batch_create": [_VP, _I32, _VP, _VP, ctypes.POINTER(np_batch_options), ctypes.POINTER(ctypes.c_void_p)],
+    "np_batch_destroy": [_VP],
+    "np_batch_layout": [_VP, _VP, ctypes.POINTER(ctypes.c_int64)],
+    "np_batch_classes": [_VP, _VP, _I32, ctypes.POINTER(ctypes.c_int32)],
+    "np_batch_set_config": [_VP, _I32, ctypes.POINTER(np_config)],
+    "np_batch_tune": [_VP, _VP, _I32, _VP],
+    "np_batch_run": [_VP, _VP, _VP, ctypes.POINTER(np_stats)],
+    "np_server_create": [_VP, _VP, _I32, ctypes.POINTER(np_server_options), ctypes.POINTER(ctypes.c_void_p)],
+    "np_server_destroy": [_VP],
+    "np_server_pool_info": [_VP, _I32, _I32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint64)],
+    "np_server_submit": [_VP, _I32, _I32, _I32, _VP, ctypes.POINTER(ctypes.c_int64)],
+    "np_server_step": [_VP, ctypes.POINTER(ctypes.c_int32)],
+    "np_server_poll": [_VP, _I64, ctypes.POINTER(np_query_info)],
     "np_status_string": [_I32],
     "np_version": [],
 }
@@ -336,6 +385,119 @@ def np_bezier_host(ctx, ctrl, ncurves: int, offsets_out, points_out, cap: int, c
 
 
 # ------------------------------------------------------------ configurations
+
+def np_bfs_multi(ctx, g: np_csr, sources, level, ld: int, cfg=None, stream=None, stats: bool = False,
+                 check: bool = True):
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+    st, want = _stats_arg(stats)
+    s = lib().np_bfs_multi(ctx, ctypes.byref(g), int(src.shape[0]), src.ctypes.data, _ptr(level), int(ld),
+                           ctypes.byref(_cfg(cfg)), _stream(stream), ctypes.byref(st) if want else None)
+    _check(s, "np_bfs_multi", check)
+    return (s, st.as_dict()) if want else s
+
+
+def np_sssp_multi(ctx, g: np_csr, sources, dist, ld: int, cfg=None, stream=None, stats: bool = False,
+                  check: bool = True):
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+    st, want = _stats_arg(stats)
+    s = lib().np_sssp_multi(ctx, ctypes.byref(g), int(src.shape[0]), src.ctypes.data, _ptr(dist), int(ld),
+                            ctypes.byref(_cfg(cfg)), _stream(stream), ctypes.byref(st) if want else None)
+    _check(s, "np_sssp_multi", check)
+    return (s, st.as_dict()) if want else s
+
+
+def multi_stride(n: int) -> int:
+    """Row stride of np_bfs_multi / np_sssp_multi outputs: the next power of two >= n."""
+    return 1 << max(0, (int(n) - 1).bit_length())
+
+
+def np_batch_create(ctx, graphs: list[np_csr], sources, kind: int, cfg=None, class_log2_width: int = 0,
+                    max_group_edges: int = 0) -> ctypes.c_void_p:
+    arr = (np_csr * len(graphs))(*graphs)
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+    opt = np_batch_options(int(kind), int(class_log2_width), int(max_group_edges), _cfg(cfg))
+    h = ctypes.c_void_p()
+    _check(lib().np_batch_create(ctx, len(graphs), ctypes.cast(arr, ctypes.c_void_p), src.ctypes.data,
+                                 ctypes.byref(opt), ctypes.byref(h)), "np_batch_create", True)
+    return h
+
+
+def np_batch_destroy(b) -> int:
+    return _check(lib().np_batch_destroy(b), "np_batch_destroy", True)
+
+
+def np_batch_layout(b, count: int) -> tuple[np.ndarray, int]:
+    off = np.zeros(count, dtype=np.int64)
+    tot = ctypes.c_int64()
+    _check(lib().np_batch_layout(b, off.ctypes.data, ctypes.byref(tot)), "np_batch_layout", True)
+    return off, int(tot.value)
+
+
+def np_batch_classes(b) -> list[dict]:
+    n = ctypes.c_int32()
+    _check(lib().np_batch_classes(b, None, 0, ctypes.byref(n)), "np_batch_classes", True)
+    arr = (np_batch_class * max(1, n.value))()
+    _check(lib().np_batch_classes(b, ctypes.cast(arr, ctypes.c_void_p), n.value, ctypes.byref(n)),
+           "np_batch_classes", True)
+    return [arr[i].as_dict() for i in range(n.value)]
+
+
+def np_batch_set_config(b, cls: int, cfg, check: bool = True) -> int:
+    return _check(lib().np_batch_set_config(b, int(cls), ctypes.byref(cfg)), "np_batch_set_config", check)
+
+
+def np_batch_tune(b, out, reps: int = 0, stream=None) -> int:
+    return _check(lib().np_batch_tune(b, _ptr(out), int(reps), _stream(stream)), "np_batch_tune", True)
+
+
+def np_batch_run(b, out, stream=None, stats: bool = False, check: bool = True):
+    st, want = _stats_arg(stats)
+    s = lib().np_batch_run(b, _ptr(out), _stream(stream), ctypes.byref(st) if want else None)
+    _check(s, "np_batch_run", check)
+    return (s, st.as_dict()) if want else s
+
+
+def np_server_create(ctx, graphs: list[np_csr], memory_budget: int = 0, max_slots: int = 0,
+                     levels_per_step: int = 0, bfs_cfg=None, sssp_cfg=None, check: bool = True):
+    arr = (np_csr * len(graphs))(*graphs)
+    opt = np_server_options(int(memory_budget), int(max_slots), int(levels_per_step), _cfg(bfs_cfg), _cfg(sssp_cfg))
+    h = ctypes.c_void_p()
+    s = lib().np_server_create(ctx, ctypes.cast(arr, ctypes.c_void_p), len(graphs), ctypes.byref(opt),
+                               ctypes.byref(h))
+    _check(s, "np_server_create", check)
+    return h if s == NP_OK else s
+
+
+def np_server_destroy(sv) -> int:
+    return _check(lib().np_server_destroy(sv), "np_server_destroy", True)
+
+
+def np_server_pool_info(sv, graph: int, kind: int) -> tuple[int, int]:
+    slots = ctypes.c_int32()
+    b = ctypes.c_uint64()
+    _check(lib().np_server_pool_info(sv, int(graph), int(kind), ctypes.byref(slots), ctypes.byref(b)),
+           "np_server_pool_info", True)
+    return int(slots.value), int(b.value)
+
+
+def np_server_submit(sv, graph: int, kind: int, src: int, out, check: bool = True) -> int:
+    t = ctypes.c_int64()
+    s = lib().np_server_submit(sv, int(graph), int(kind), int(src), _ptr(out), ctypes.byref(t))
+    _check(s, "np_server_submit", check)
+    return int(t.value) if s == NP_OK else -s
+
+
+def np_server_step(sv, check: bool = True) -> int:
+    k = ctypes.c_int32()
+    _check(lib().np_server_step(sv, ctypes.byref(k)), "np_server_step", check)
+    return int(k.value)
+
+
+def np_server_poll(sv, ticket: int) -> dict:
+    q = np_query_info()
+    _check(lib().np_server_poll(sv, int(ticket), ctypes.byref(q)), "np_server_poll", True)
+    return q.as_dict()
+
 
 def config(form: str = "tca", **kw) -> np_config:
     """Named forms of the paper's evaluation: 'nodp', 'cdp' (plain device launch),

@@ -59,6 +59,10 @@ int main(void) {
   printf("np_parents %zu %zu %zu\n", sizeof(np_parents), offsetof(np_parents, ids), offsetof(np_parents, count));
   printf("np_body %zu %zu %zu\n", sizeof(np_body), offsetof(np_body, level), offsetof(np_body, cap));
   printf("np_profile %zu %zu %zu\n", sizeof(np_profile), offsetof(np_profile, levels), offsetof(np_profile, level_child_ms));
+  printf("np_batch_options %zu %zu %zu\n", sizeof(np_batch_options), offsetof(np_batch_options, max_group_edges), offsetof(np_batch_options, config));
+  printf("np_batch_class %zu %zu %zu\n", sizeof(np_batch_class), offsetof(np_batch_class, config), offsetof(np_batch_class, candidates));
+  printf("np_server_options %zu %zu %zu\n", sizeof(np_server_options), offsetof(np_server_options, levels_per_step), offsetof(np_server_options, sssp_config));
+  printf("np_query_info %zu %zu %zu\n", sizeof(np_query_info), offsetof(np_query_info, slot), offsetof(np_query_info, finish_step));
   return 0;
 }
 ''')
@@ -72,13 +76,17 @@ int main(void) {
         "np_parents": (npb.np_parents, "ids", "count"),
         "np_body": (npb.np_body, "level", "cap"),
         "np_profile": (npb.np_profile, "levels", "level_child_ms"),
+        "np_batch_options": (npb.np_batch_options, "max_group_edges", "config"),
+        "np_batch_class": (npb.np_batch_class, "config", "candidates"),
+        "np_server_options": (npb.np_server_options, "levels_per_step", "sssp_config"),
+        "np_query_info": (npb.np_query_info, "slot", "finish_step"),
     }
     for name, (cls, f1, f2) in py.items():
         assert rows[name] == [ctypes.sizeof(cls), getattr(cls, f1).offset, getattr(cls, f2).offset], name
 
 
 def test_host_only_entry_points(lib):
-    assert npb.np_version() == 10000
+    assert npb.np_version() == 10100
     assert npb.np_status_string(npb.NP_ERR_INVALID) == "invalid argument"
     cfg = npb.np_config_default()
     assert (cfg.variant, cfg.threshold, cfg.cfactor, cfg.granularity, cfg.scan) == (1, 32, 8, npb.NP_GRAN_GRID_HOST, npb.NP_SCAN_ATOMIC)
@@ -89,6 +97,19 @@ def test_host_only_entry_points(lib):
     bad = cfg.replace(cfactor=3)
     with pytest.raises(npb.NestparError):
         npb.np_workspace_size(10, bad)
+
+
+def test_host_argument_errors_of_new_entry_points(lib):
+    """Argument checks that return before any device work (NULL handles, bad sizes)."""
+    L = npb.lib()
+    assert L.np_batch_destroy(None) == npb.NP_ERR_INVALID
+    assert L.np_server_destroy(None) == npb.NP_ERR_INVALID
+    assert L.np_server_step(None, None) == npb.NP_ERR_INVALID
+    assert L.np_batch_run(None, None, None, None) == npb.NP_ERR_INVALID
+    assert L.np_batch_create(None, 0, None, None, None, None) == npb.NP_ERR_INVALID
+    assert L.np_server_create(None, None, 0, None, None) == npb.NP_ERR_INVALID
+    assert L.np_bfs_multi(None, None, 0, None, None, 0, None, None, None) == npb.NP_ERR_INVALID
+    assert npb.multi_stride(1) == 1 and npb.multi_stride(4096) == 4096 and npb.multi_stride(4097) == 8192
 
 
 def test_named_forms():
