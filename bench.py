@@ -17,7 +17,12 @@ Other workloads (--workload): bfs-rmat20 (BFS on the same graph), bfs4k (the
 4096-vertex power-law digraph), road (a 264K-vertex grid road graph with
 out-degree <= 8: the low-nested-parallelism case, with the never-taken launch
 site measured against the same kernel without it), bt64k (Bezier tessellation
-of 65,536 curves, points/s).
+of 65,536 curves, points/s), batched-sssp / batched-bfs (512 R-MAT instances,
+n log-uniform in [2^10, 2^20], edge factor 8..32, in one CUDA graph launch
+per step after the per-size-class autotuner; total GTEPS), serving (Poisson
+arrivals of BFS/SSSP queries from random sources over seven resident R-MAT
+graphs of scales 16..22; queries/s at saturation and p50/p99 latency at
+0.5/0.8/0.95 of it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 """
@@ -53,6 +58,18 @@ WORKLOADS = {
     "road": dict(kind="sssp", graph="road",
                  config=dict(workload="sssp_road_grid_264k", vertices=514 * 514, degrees="2..8 (grid, diagonals p=1/2)",
                              weights="uint32 uniform [1,255]", source=0, seed=6)),
+    "batched-sssp": dict(kind="batched", batch_kind=1,
+                         config=dict(workload="batched_sssp_512_rmat_instances", instances=512,
+                                     vertices="log-uniform [2^10, 2^20]", edge_factor="uniform [8, 32]",
+                                     weights="uint32 uniform [1,255]", source=0, seed=4)),
+    "batched-bfs": dict(kind="batched", batch_kind=0,
+                        config=dict(workload="batched_bfs_512_rmat_instances", instances=512,
+                                    vertices="log-uniform [2^10, 2^20]", edge_factor="uniform [8, 32]",
+                                    source=0, seed=4)),
+    "serving": dict(kind="serving",
+                    config=dict(workload="serving_bfs_sssp_queries_rmat_scales_16_22", graphs="R-MAT scales 16..22",
+                                edge_factor=16, weights="uint32 uniform [1,255]", mix="50/50 BFS/SSSP",
+                                arrivals="Poisson", seed=5)),
     "bt64k": dict(kind="bezier", graph=None,
                   config=dict(workload="bezier_tessellation_65536_curves", curves=65536,
                               points="ceil(sqrt(kappa)*64) clamped to [4,4096]", seed=3)),
@@ -246,6 +263,8 @@ def run_reference(args, ws, rank):
         return
     import oracle
     wl = WORKLOADS[args.workload]
+    if wl["kind"] in ("batched", "serving"):
+        return run_reference_multi(args, ws, wl)
     if wl["kind"] == "bezier":
         from paper_2201_02789_gb300 import gen
         ctrl = gen.bt64k()
@@ -574,6 +593,378 @@ def run_ours(args, ws, rank, local):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------- batched and serving
+
+def batch_inputs(batch_kind: int):
+    from paper_2201_02789_gb300 import build as nbuild
+    from paper_2201_02789_gb300 import gen
+    nbuild.build_gen()
+    specs = gen.batch_specs(512, seed=4)
+    graphs = gen.batch_graphs(specs, weights=(1, 255) if batch_kind == 1 else None)
+    return specs, graphs
+
+
+def serving_graphs():
+    from paper_2201_02789_gb300 import build as nbuild
+    from paper_2201_02789_gb300 import gen
+    from concurrent.futures import ThreadPoolExecutor
+    nbuild.build_gen()
+    with ThreadPoolExecutor(7) as ex:
+        return list(ex.map(lambda s: gen.rmat(s, 16, seed=5 * 1000 + s), range(16, 23)))
+
+
+def serving_queries(graphs, count: int, seed: int):
+    """(graph, kind, source) per query: graph and kind uniform, source uniform over vertices with edges."""
+    from paper_2201_02789_gb300 import gen
+    gi = gen.uniform_int(seed, gen.S_SOURCE + 10, 0, count, 0, len(graphs) - 1)
+    kinds = gen.uniform_int(seed, gen.S_SOURCE + 11, 0, count, 0, 1)
+    out = []
+    for q in range(count):
+        g = graphs[int(gi[q])]
+        src = int(gen.random_sources(g, 1, seed=seed * 100003 + q)[0])
+        out.append((int(gi[q]), int(kinds[q]), src))
+    return out
+
+
+def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson process: exponential gaps from the seeded uniform stream."""
+    from paper_2201_02789_gb300 import gen
+    u = gen.uniform_f64(seed, gen.S_SOURCE + 12, 0, count)
+    return np.cumsum(-np.log1p(-u) / rate)
+
+
+def run_reference_multi(args, ws, wl):
+    """Reference arm for the batched and serving workloads: the oracle, one query or
+    instance after another, on a bounded sample of the workload per step."""
+    import oracle
+    if wl["kind"] == "batched":
+        specs, graphs = batch_inputs(wl["batch_kind"])
+        order = np.argsort([g.n for g in graphs], kind="stable")
+        sample = [int(order[k]) for k in np.linspace(0, len(order) - 1, 24).astype(int)]
+
+        def run():
+            u = 0
+            for i in sample:
+                g = graphs[i]
+                if wl["batch_kind"] == 1:
+                    d = oracle.sssp(g.row_ptr, g.col, g.w, 0)
+                    u += reached_edges(g, d != 0xFFFFFFFF)
+                else:
+                    lv = oracle.bfs(g.row_ptr, g.col, 0)
+                    u += reached_edges(g, lv >= 0)
+            return u
+        unit, what = "GTEPS", f"24 of the 512 instances per step, spread over the size range"
+    else:
+        graphs = serving_graphs()
+        qs = serving_queries(graphs, 64, seed=55)
+
+        def run():
+            for gi, kind, src in qs:
+                g = graphs[gi]
+                if kind == 1:
+                    oracle.sssp(g.row_ptr, g.col, g.w, src)
+                else:
+                    oracle.bfs(g.row_ptr, g.col, src)
+            return len(qs)
+        unit, what = "queries/s", "64 queries per step, answered one after another"
+    for _ in range(min(args.warmup, 1)):
+        run()
+    ts, units = [], 0
+    steps = min(args.steps, 5)
+    for _ in range(steps):
+        t = time.perf_counter()
+        units = run()
+        ts.append(time.perf_counter() - t)
+    total = sum(ts)
+    value = steps * units / total / (1e9 if unit == "GTEPS" else 1.0)
+    line = {"impl": "reference", "metric": f"{unit} ({args.workload})", "value": value, "unit": unit,
+            "n_gpus": ws, "steps": steps, "warmup": args.warmup, "ms_per_step": total / steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": dict(wl["config"], l2="n/a (host)"),
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": what},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args, ws, rank, local, wl):
+    import torch
+    import oracle
+    from paper_2201_02789_gb300 import nestpar as npb
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
+    bk = wl["batch_kind"]
+    t_gen = time.perf_counter()
+    specs, graphs = batch_inputs(bk)
+    t_gen = time.perf_counter() - t_gen
+    log(f"generated {len(graphs)} instances, {sum(g.m for g in graphs)} edges in {t_gen:.1f} s")
+    ctx = npb.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.int8, device=dev)
+
+    def upload():
+        tens = []
+        for g in graphs:
+            rp = torch.from_numpy(g.row_ptr).to(dev, non_blocking=True)
+            col = torch.from_numpy(g.col).to(dev, non_blocking=True)
+            w = torch.from_numpy(g.w.view(np.int32)).to(dev, non_blocking=True) if bk == 1 else None
+            tens.append((rp, col, w))
+        return tens, [npb.make_csr(rp, col, w, n=g.n, m=g.m) for (rp, col, w), g in zip(tens, graphs)]
+
+    tens, csrs = upload()
+    torch.cuda.synchronize(dev)
+    srcs = np.zeros(len(graphs), dtype=np.int32)
+    b = npb.np_batch_create(ctx.handle, csrs, srcs, bk, npb.config("tca"))
+    offs, total = npb.np_batch_layout(b, len(graphs))
+    del tens, csrs
+    torch.cuda.empty_cache()
+    out = torch.empty((total,), dtype=torch.int32, device=dev)
+
+    def timed(steps):
+        return time_solves(lambda: npb.np_batch_run(b, out, stream=stream), steps, flush, stream)
+
+    # untuned (every class on the library default), then the autotuner
+    for _ in range(3):
+        npb.np_batch_run(b, out, stream=stream)
+    ms_default = statistics.median(timed(max(3, args.steps // 4)))
+    t_tune = time.perf_counter()
+    npb.np_batch_tune(b, out, reps=3, stream=stream)
+    t_tune = time.perf_counter() - t_tune
+    classes = npb.np_batch_classes(b)
+    for _ in range(max(args.warmup, 3)):
+        npb.np_batch_run(b, out, stream=stream)
+    _, st = npb.np_batch_run(b, out, stream=stream, stats=True)
+    res = out.cpu().numpy()
+    res = res.view(np.uint32) if bk == 1 else res
+    units = 0
+    for i, g in enumerate(graphs):
+        r = res[offs[i]:offs[i] + g.n]
+        units += reached_edges(g, (r != 0xFFFFFFFF) if bk == 1 else (r >= 0))
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize(dev)
+    sampler.mark("t0")
+    ms = timed(args.steps)
+    torch.cuda.synchronize(dev)
+    sampler.mark("t1")
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(sum(ms), dev)
+    value = job_value(ws, args.steps, units, total_ms)
+    if rank != 0:
+        npb.np_batch_destroy(b)
+        ctx.close()
+        return
+
+    # the same instances one solve after another through np_bfs / np_sssp (no batching)
+    seq_ms = None
+    if not args.only_headline:
+        one = torch.empty((max(g.n for g in graphs),), dtype=torch.int32, device=dev)
+        devg = []
+        for g in graphs:
+            rp = torch.from_numpy(g.row_ptr).to(dev)
+            col = torch.from_numpy(g.col).to(dev)
+            w = torch.from_numpy(g.w.view(np.int32)).to(dev) if bk == 1 else None
+            devg.append((npb.make_csr(rp, col, w, n=g.n, m=g.m), rp, col, w))
+        f = npb.np_sssp if bk == 1 else npb.np_bfs
+        cfg = npb.config("tca")
+
+        def seq():
+            for c, *_ in devg:
+                f(ctx.handle, c, 0, one, cfg, stream=stream)
+        seq()
+        seq_ms = statistics.median(time_solves(seq, 3, flush, stream))
+        del devg
+        torch.cuda.empty_cache()
+
+    # parity on a sample of instances (the oracle, on host cores) and the CPU baseline
+    order = np.argsort([g.n for g in graphs], kind="stable")
+    sample = sorted({int(order[k]) for k in np.linspace(0, len(order) - 1, 16).astype(int)})
+    t_cpu, cpu_units, parity = 0.0, 0, True
+    for i in sample:
+        g = graphs[i]
+        t = time.perf_counter()
+        ref = oracle.sssp(g.row_ptr, g.col, g.w, 0) if bk == 1 else oracle.bfs(g.row_ptr, g.col, 0)
+        t_cpu += time.perf_counter() - t
+        cpu_units += reached_edges(g, (ref != 0xFFFFFFFF) if bk == 1 else (ref >= 0))
+        parity = parity and bool(np.array_equal(ref, res[offs[i]:offs[i] + g.n]))
+    cpu = {"value": cpu_units / t_cpu / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+           "sample": f"{len(sample)} instances spread over the size range ({t_cpu:.1f} s)"}
+
+    # end to end: host graphs in (pinned), batch build, one launch, results out
+    pinned = [(torch.from_numpy(g.row_ptr).pin_memory(), torch.from_numpy(g.col).pin_memory(),
+               torch.from_numpy(g.w.view(np.int32)).pin_memory() if bk == 1 else None) for g in graphs]
+    out_h = torch.empty((total,), dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for k in range(3):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        dt = [(rp.to(dev, non_blocking=True), col.to(dev, non_blocking=True),
+               w.to(dev, non_blocking=True) if w is not None else None) for rp, col, w in pinned]
+        cs = [npb.make_csr(rp, col, w, n=g.n, m=g.m) for (rp, col, w), g in zip(dt, graphs)]
+        torch.cuda.synchronize(dev)
+        b2 = npb.np_batch_create(ctx.handle, cs, srcs, bk, npb.config("tca"))
+        for ci, c in enumerate(classes):
+            npb.np_batch_set_config(b2, ci, npb.np_config(**c["config"]))
+        del dt, cs
+        npb.np_batch_run(b2, out, stream=stream)
+        out_h.copy_(out, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append((time.perf_counter() - t) * 1e3)
+        npb.np_batch_destroy(b2)
+    h2d = sum(4 * (g.n + 1) + (8 if bk == 1 else 4) * g.m for g in graphs)
+    e2e = {"value": units / (statistics.median(e2e_ms) * 1e-3) / 1e9, "unit": "GTEPS",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(4 * total),
+           "ms_per_step": statistics.median(e2e_ms), "includes": "graph upload, np_batch_create (union copies, "
+           "workspaces), tuned configs applied, one np_batch_run, result read-back",
+           "matches_device_result": bool(np.array_equal(out_h.numpy().view(res.dtype), res))}
+
+    # algorithmic bytes (per instance, as the single-solve model) over the batch time
+    kb = kernel_bytes("sssp" if bk == 1 else "bfs", st)
+    peak, peak_kind = hbm_peak()
+    med = statistics.median(ms)
+    step_bytes = kb["solve"]
+    groups = sum(c["groups"] for c in classes)
+    per_iter = 2 * 4 + 1
+    gpu_launches = int(args.steps * (2 * groups + st["graph_iterations"] * per_iter))
+    line = {"metric": f"GTEPS and ms/batch ({args.workload}): 512 instances in one graph launch, autotuned per "
+                      f"size class", "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": dict(wl["config"], edges=int(sum(g.m for g in graphs)), vertices_total=int(total),
+                           l2="inputs (%.1f GB) larger than L2; also flushed between steps"
+                              % (sum(g.m for g in graphs) * (8 if bk == 1 else 4) / 1e9)),
+            "ms_per_batch": {"median": med, "min": min(ms)}, "units_per_batch": units,
+            "untuned_ms_per_batch": ms_default, "tune_seconds": t_tune,
+            "sequential_solves_ms": seq_ms,
+            "speedup_vs_sequential": (seq_ms / med) if seq_ms else None,
+            "classes": [{"log2_n": [c["log2_lo"], c["log2_lo"] + 2], "instances": c["instances"],
+                         "groups": c["groups"], "edges": c["edges"], "tuned_ms": c["tuned_ms"],
+                         "threshold": c["config"]["threshold"], "cfactor": c["config"]["cfactor"],
+                         "child_block": c["config"]["child_block"],
+                         "form": "nodp" if c["config"]["variant"] == 0 else "grid_host_aggregation"}
+                        for c in classes],
+            "step_roofline": {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (med * 1e-3) / 1e9,
+                              "frac": step_bytes / (med * 1e-3) / 1e9 / peak, "peak": peak, "peak_kind": peak_kind},
+            "cpu_baseline": cpu, "parity_vs_oracle_sample": parity, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": gpu_launches, "generation_seconds": t_gen}
+    print(json.dumps(line), flush=True)
+    npb.np_batch_destroy(b)
+    ctx.close()
+
+
+def run_serving(args, ws, rank, local, wl):
+    import torch
+    import oracle
+    from paper_2201_02789_gb300 import nestpar as npb
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
+    graphs = serving_graphs()
+    ctx = npb.Context(local)
+    devs = []
+    for g in graphs:
+        rp = torch.from_numpy(g.row_ptr).to(dev)
+        col = torch.from_numpy(g.col).to(dev)
+        w = torch.from_numpy(g.w.view(np.int32)).to(dev)
+        devs.append((npb.make_csr(rp, col, w, n=g.n, m=g.m), rp, col, w))
+    lps = 2
+    sv = npb.np_server_create(ctx.handle, [d[0] for d in devs], max_slots=64, levels_per_step=lps,
+                              bfs_cfg=npb.config("tca"), sssp_cfg=npb.config("tca"))
+    slots = {(gi, k): npb.np_server_pool_info(sv, gi, k) for gi in range(len(graphs)) for k in (0, 1)}
+
+    def run_load(queries, arrivals):
+        """Submits query q at arrivals[q] (s from the start; None = all at once), steps the
+        server until every query is done; returns per-query latency (ms), wall time and steps."""
+        outs, tick, t_done, by_ticket = {}, {}, {}, {}
+        n = len(queries)
+        t0 = time.perf_counter()
+        nxt, steps = 0, 0
+        live = set()
+        while len(t_done) < n:
+            now = time.perf_counter() - t0
+            while nxt < n and (arrivals is None or arrivals[nxt] <= now):
+                gi, kind, src = queries[nxt]
+                outs[nxt] = torch.empty((graphs[gi].n,), dtype=torch.int32, device=dev)
+                tick[nxt] = npb.np_server_submit(sv, gi, kind, src, outs[nxt])
+                by_ticket[tick[nxt]] = nxt
+                live.add(nxt)
+                nxt += 1
+            if not live:
+                time.sleep(max(0.0, min(arrivals[nxt] - now, 0.001)) if arrivals is not None else 0)
+                continue
+            npb.np_server_step(sv)
+            steps += 1
+            t = time.perf_counter() - t0
+            for tk in npb.np_server_finished(sv):
+                q = by_ticket.pop(tk)
+                t_done[q] = t
+                live.discard(q)
+                if q >= 24:          # keep a few results for the parity check
+                    outs.pop(q)
+        wall = time.perf_counter() - t0
+        arr = np.zeros(n) if arrivals is None else np.asarray(arrivals)
+        lat = np.array([(t_done[q] - arr[q]) * 1e3 for q in range(n)])
+        return lat, wall, steps, outs
+
+    # saturation: everything submitted at once (closed loop)
+    warm = serving_queries(graphs, 64, seed=51)
+    run_load(warm, None)
+    sat_q = serving_queries(graphs, 512, seed=52)
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize(dev)
+    sampler.mark("t0")
+    lat_sat, wall_sat, steps_sat, outs = run_load(sat_q, None)
+    torch.cuda.synchronize(dev)
+    sampler.mark("t1")
+    clocks = sampler.stop()
+    qps_sat = len(sat_q) / wall_sat
+    # parity: the first retained results against the oracle, and alone (np_bfs / np_sssp) vs the mix
+    parity = True
+    alone_eq = True
+    for q in sorted(outs)[:24]:
+        gi, kind, src = sat_q[q]
+        g = graphs[gi]
+        got = outs[q].cpu().numpy()
+        ref = oracle.sssp(g.row_ptr, g.col, g.w, src) if kind else oracle.bfs(g.row_ptr, g.col, src)
+        parity = parity and bool(np.array_equal(got.view(np.uint32) if kind else got, ref))
+        alone = torch.empty((g.n,), dtype=torch.int32, device=dev)
+        (npb.np_sssp if kind else npb.np_bfs)(ctx.handle, devs[gi][0], src, alone, npb.config("tca"))
+        alone_eq = alone_eq and bool(torch.equal(alone, outs[q]))
+    loads = {}
+    for frac in (0.5, 0.8, 0.95):
+        nq = max(64, min(400, int(qps_sat * frac * 2.0)))
+        qs = serving_queries(graphs, nq, seed=int(60 + frac * 100))
+        arr = poisson_arrivals(qps_sat * frac, nq, seed=int(70 + frac * 100))
+        lat, wall, steps, _ = run_load(qs, arr)
+        loads[str(frac)] = {"offered_qps": qps_sat * frac, "achieved_qps": nq / wall, "queries": nq,
+                            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                            "steps": steps}
+    npb.np_server_destroy(sv)
+    ctx.close()
+    if rank != 0:
+        return
+    kernels_per_pool_step = 5 + 2 * lps
+    line = {"metric": "queries/s at saturation and p50/p99 latency (serving): continuous batching of BFS/SSSP "
+                      "queries over resident R-MAT graphs", "value": qps_sat * ws, "unit": "queries/s",
+            "n_gpus": ws, "steps": steps_sat, "warmup": 1, "ms_per_step": wall_sat / steps_sat * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": dict(wl["config"], edges=int(sum(g.m for g in graphs)), levels_per_step=lps,
+                           max_slots=64, l2="graphs (%.1f GB) larger than L2" % (
+                               sum(g.m for g in graphs) * 8 / 1e9)),
+            "saturation": {"queries": len(sat_q), "seconds": wall_sat, "p50_ms": float(np.percentile(lat_sat, 50)),
+                           "p99_ms": float(np.percentile(lat_sat, 99))},
+            "poisson": loads,
+            "slots": {f"scale{16 + gi}_{'sssp' if k else 'bfs'}": slots[(gi, k)][0] for (gi, k) in slots},
+            "parity_vs_oracle_sample": parity, "alone_equals_mix": alone_eq,
+            "e2e": {"value": qps_sat * ws, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0, "note": "host-driven loop: every step ends in a host read-back"},
+            "clocks": clocks, "gpu_launches_per_pool_step": kernels_per_pool_step}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -593,6 +984,12 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    wl = WORKLOADS[args.workload]
+    if wl["kind"] == "batched":
+        run_batched(args, ws, rank, local, wl)
+    elif wl["kind"] == "serving":
+        run_serving(args, ws, rank, local, wl)
     else:
         run_ours(args, ws, rank, local)
 

@@ -198,7 +198,10 @@ np_status np_sssp_multi(np_ctx *ctx, const np_csr *g, int32_t nsrc, const int32_
  * sit in a conditional body: NP_VARIANT_NODP, or NP_VARIANT_CDP with
  * NP_GRAN_GRID_HOST (others get NP_ERR_UNSUPPORTED). The batch owns its union
  * copies (device memory about the inputs' size) and workspaces; the inputs
- * may be freed after np_batch_create returns. */
+ * may be freed after np_batch_create returns. np_batch_create first waits
+ * for the device (the inputs may come from any stream), then checks every
+ * graph on the GPU (row_ptr[0] = 0, non-decreasing, row_ptr[n] = m, column
+ * indices in [0, n)) and returns NP_ERR_INVALID if one breaks that. */
 #define NP_BATCH_BFS 0
 #define NP_BATCH_SSSP 1
 typedef struct np_batch_options {
@@ -258,7 +261,9 @@ np_status np_batch_run(np_batch *b, void *out, void *stream, np_stats *stats);
  * copies finished queries (no entries left) to their `out` arrays, all as
  * one CUDA graph per pool on the pool's own stream, so pools overlap on the
  * device; then it waits and marks finished queries done. Results equal
- * np_bfs / np_sssp from the same source. */
+ * np_bfs / np_sssp from the same source. np_server_create waits for the
+ * device and checks every graph as np_batch_create does. An `out` array must
+ * not be touched by other work until its query is done. */
 typedef struct np_server_options {
   uint64_t memory_budget;     /* bytes for slot state (0 = a quarter of free device memory) */
   int32_t max_slots;          /* per pool (0 = 64) */
@@ -292,6 +297,9 @@ np_status np_server_submit(np_server *s, int32_t graph, int32_t kind, int32_t sr
 /* One serving round (see above). *in_flight = queries queued or resident after it. */
 np_status np_server_step(np_server *s, int32_t *in_flight);
 np_status np_server_poll(const np_server *s, int64_t ticket, np_query_info *info);
+/* Moves up to `max` tickets of queries finished since the last call (oldest
+ * first) into tickets[]; *count = how many. */
+np_status np_server_finished(np_server *s, int64_t *tickets, int32_t max, int32_t *count);
 
 /* Quadratic Bezier tessellation (Section VII, BT benchmark). ctrl is
  * float[ncurves][3][2]. Parent = curve c with curvature

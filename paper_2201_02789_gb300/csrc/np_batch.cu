@@ -310,8 +310,21 @@ np_status np_batch_create(np_ctx* ctx, int32_t count, const np_csr* graphs, cons
     b->classes.push_back(c);
   }
   b->total = vbase;
-  // union copies
+  // The inputs may have been written by any stream: wait for the device, then
+  // check every graph before anything indexes it.
   cudaStream_t s = b->e.cap_stream;
+  {
+    int* scratch = nullptr;
+    st = from_cuda(cudaDeviceSynchronize());
+    if (st == NP_OK) st = from_cuda(cudaMalloc(&scratch, sizeof(int)));
+    if (st == NP_OK) st = check_csr_device(graphs, count, scratch, s);
+    if (scratch) cudaFree(scratch);
+    if (st != NP_OK) {
+      np_batch_destroy(b);
+      return st;
+    }
+  }
+  // union copies
   for (Group& g : b->groups) {
     g.nsrc = (int)g.members.size();
     const size_t brp = align_up(sizeof(int) * ((size_t)g.n + 1)), bcol = align_up(sizeof(int) * (size_t)g.m);

@@ -99,6 +99,21 @@ __global__ void seed_sources_kernel(LevelState* st, int kind, const int* ids, in
   }
 }
 
+__global__ void csr_check_kernel(const int* row_ptr, const int* col, int n, long long m, int* bad) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long top = n > m ? (long long)n : m;
+  bool ok = true;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < top; i += stride) {
+    if (i < n) ok = ok && row_ptr[i] <= row_ptr[i + 1];
+    if (i < m) {
+      const int v = col[i];
+      ok = ok && v >= 0 && v < n;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ok = ok && row_ptr[0] == 0 && (long long)row_ptr[n] == m;
+  if (!ok) atomicOr(bad, 1);
+}
+
 // Between graph bodies or chunks: the next body position 0 is level base + K.
 __global__ void advance_base_kernel(LevelState* st, int K) { st->base += K; }
 
@@ -589,6 +604,20 @@ np_status run_levels(Engine& e, Workspace& w, const Plan& p, const Args& a, cons
     if (count <= 0 || level >= max_levels) break;
   }
   return NP_OK;
+}
+
+np_status check_csr_device(const np_csr* graphs, int count, int* scratch, cudaStream_t s) {
+  NP_CK(cudaMemsetAsync(scratch, 0, sizeof(int), s));
+  for (int i = 0; i < count; i++) {
+    const np_csr& g = graphs[i];
+    const long long top = g.n > g.m ? (long long)g.n : g.m;
+    csr_check_kernel<<<blocks_for(top), 256, 0, s>>>(g.row_ptr, g.col_idx, g.n, g.m, scratch);
+    NP_CK(cudaGetLastError());
+  }
+  int bad = 0;
+  NP_CK(cudaMemcpyAsync(&bad, scratch, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NP_CK(cudaStreamSynchronize(s));
+  return bad ? NP_ERR_INVALID : NP_OK;
 }
 
 np_status check_csr(const np_csr* g, bool need_w) {

@@ -149,6 +149,12 @@ __global__ void fill_unreached_kernel(int kind, long long total, int* level, uns
 __global__ void seed_sources_kernel(LevelState* st, int kind, const int* ids, int nsrc, int* level, unsigned* dist,
                                     int* fr0, int max_levels);
 __global__ void advance_base_kernel(LevelState* st, int K);
+// Sets *bad when a CSR breaks its contract: row_ptr[0] != 0, row_ptr[n] != m,
+// a decreasing row_ptr, or a column index outside [0, n).
+__global__ void csr_check_kernel(const int* row_ptr, const int* col, int n, long long m, int* bad);
+// Runs csr_check_kernel over each graph on stream s and waits: NP_ERR_INVALID
+// if any breaks the contract. `scratch` is one device int.
+np_status check_csr_device(const np_csr* graphs, int count, int* scratch, cudaStream_t s);
 
 inline int blocks_for(long long n, int per = 256, int cap = 4096) {
   long long b = (n + per - 1) / per;

@@ -183,6 +183,7 @@ struct np_server {
   std::vector<Query> queries;
   int levels_per_step = 2;
   int64_t step = 0;
+  std::vector<int64_t> finished;    // tickets finished since the last np_server_finished
   std::mutex mu;
 };
 
@@ -325,6 +326,14 @@ np_status np_server_create(np_ctx* ctx, const np_csr* graphs, int32_t ngraphs, c
   np_server* sv = new np_server();
   sv->levels_per_step = lps;
   np_status st = engine_init(sv->e, device);
+  // the graphs may have been written by any stream: wait, then check each once
+  if (st == NP_OK) {
+    int* scratch = nullptr;
+    st = from_cuda(cudaDeviceSynchronize());
+    if (st == NP_OK) st = from_cuda(cudaMalloc(&scratch, sizeof(int)));
+    if (st == NP_OK) st = check_csr_device(graphs, ngraphs, scratch, sv->e.cap_stream);
+    if (scratch) cudaFree(scratch);
+  }
   const int npools = 2 * ngraphs;
   const uint64_t share = budget / (uint64_t)npools;
   for (int gi = 0; gi < ngraphs && st == NP_OK; gi++) {
@@ -444,6 +453,7 @@ np_status np_server_step(np_server* sv, int32_t* in_flight) {
       Query& q = sv->queries[(size_t)p.slot_query[(size_t)s]];
       q.done = 1;
       q.finish_step = sv->step;
+      sv->finished.push_back(p.slot_query[(size_t)s]);
       busy[s] = 0;
       p.slot_query[(size_t)s] = -1;
     }
@@ -464,6 +474,16 @@ np_status np_server_step(np_server* sv, int32_t* in_flight) {
     *in_flight = (int32_t)k;
   }
   return worst;
+}
+
+np_status np_server_finished(np_server* sv, int64_t* tickets, int32_t max, int32_t* count) {
+  if (!sv || !count || max < 0 || (max > 0 && !tickets)) return NP_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  const int k = (int)std::min<size_t>((size_t)max, sv->finished.size());
+  if (k) std::memcpy(tickets, sv->finished.data(), sizeof(int64_t) * (size_t)k);
+  sv->finished.erase(sv->finished.begin(), sv->finished.begin() + k);
+  *count = k;
+  return NP_OK;
 }
 
 np_status np_server_poll(const np_server* sv, int64_t ticket, np_query_info* info) {

@@ -180,6 +180,7 @@ _SIGS = {
     "np_server_submit": [_VP, _I32, _I32, _I32, _VP, ctypes.POINTER(ctypes.c_int64)],
     "np_server_step": [_VP, ctypes.POINTER(ctypes.c_int32)],
     "np_server_poll": [_VP, _I64, ctypes.POINTER(np_query_info)],
+    "np_server_finished": [_VP, _VP, _I32, ctypes.POINTER(ctypes.c_int32)],
     "np_status_string": [_I32],
     "np_version": [],
 }
@@ -497,6 +498,13 @@ def np_server_poll(sv, ticket: int) -> dict:
     q = np_query_info()
     _check(lib().np_server_poll(sv, int(ticket), ctypes.byref(q)), "np_server_poll", True)
     return q.as_dict()
+
+
+def np_server_finished(sv, max_count: int = 4096) -> list[int]:
+    buf = np.zeros(max(1, max_count), dtype=np.int64)
+    k = ctypes.c_int32()
+    _check(lib().np_server_finished(sv, buf.ctypes.data, int(max_count), ctypes.byref(k)), "np_server_finished", True)
+    return buf[:k.value].tolist()
 
 
 def config(form: str = "tca", **kw) -> np_config:

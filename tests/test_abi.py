@@ -105,6 +105,7 @@ def test_host_argument_errors_of_new_entry_points(lib):
     assert L.np_batch_destroy(None) == npb.NP_ERR_INVALID
     assert L.np_server_destroy(None) == npb.NP_ERR_INVALID
     assert L.np_server_step(None, None) == npb.NP_ERR_INVALID
+    assert L.np_server_finished(None, None, 0, None) == npb.NP_ERR_INVALID
     assert L.np_batch_run(None, None, None, None) == npb.NP_ERR_INVALID
     assert L.np_batch_create(None, 0, None, None, None, None) == npb.NP_ERR_INVALID
     assert L.np_server_create(None, None, 0, None, None) == npb.NP_ERR_INVALID

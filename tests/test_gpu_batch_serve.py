@@ -152,6 +152,27 @@ def test_batch_tune_then_run(ctx):
         npb.np_batch_destroy(b)
 
 
+def test_create_checks_graphs_on_device(ctx):
+    """A column index outside [0, n) or a row_ptr that breaks its contract is refused by
+    np_batch_create / np_server_create before any traversal reads it."""
+    g = gen.rmat(9, 8, seed=45)
+    good = DevGraph(g)
+    bad_col = g.col.copy()
+    bad_col[17] = g.n                      # one past the last vertex
+    bad = DevGraph(gen.Csr(g.n, g.row_ptr, bad_col, g.w))
+    bad_rp = g.row_ptr.copy()
+    bad_rp[5], bad_rp[6] = bad_rp[6], bad_rp[5] - 1     # decreasing
+    bad2 = DevGraph(gen.Csr(g.n, bad_rp, g.col, g.w))
+    for dg in (bad, bad2):
+        with pytest.raises(npb.NestparError) as e:
+            npb.np_batch_create(ctx.handle, [good.csr, dg.csr], [0, 0], npb.NP_BATCH_BFS, npb.config("tca"))
+        assert e.value.status == npb.NP_ERR_INVALID
+        s = npb.np_server_create(ctx.handle, [good.csr, dg.csr], check=False)
+        assert s == npb.NP_ERR_INVALID
+    b = npb.np_batch_create(ctx.handle, [good.csr], [0], npb.NP_BATCH_BFS, npb.config("tca"))
+    npb.np_batch_destroy(b)
+
+
 @pytest.mark.slow
 def test_batch_full_size_sampled(ctx):
     """512 instances, n log-uniform in [2^10, 2^20], edge factor 8..32 (about 1.7e9 edges),
@@ -217,6 +238,9 @@ def test_server_alone_equals_mix(ctx, serve_graphs):
             steps += 1
             assert steps < 10000
         infos = {qi: npb.np_server_poll(sv, t) for qi, t in tickets.items()}
+        fin = npb.np_server_finished(sv)
+        assert sorted(fin) == sorted(tickets.values())        # every ticket reported once
+        assert npb.np_server_finished(sv) == []
         # queries overlapped: some were admitted while others were resident
         assert any(i["admit_step"] > i["submit_step"] for i in infos.values())
         for qi, (gi, kind, s) in enumerate(queries):
