@@ -424,16 +424,22 @@ def comparison_forms(npb, workload: str, cdp_steps: int):
         # the pair below differs only in the launch site: same CTA-tiled kernel,
         # same host-replayed chunk driver
         chunk = dict(driver=npb.NP_DRIVER_CHUNK)
+        persist = dict(driver=npb.NP_DRIVER_PERSISTENT)
         return [("nodp", npb.config("nodp"), 5),
+                ("nodp_persistent", npb.config("nodp", **persist), 5),
+                ("t_c_a_persistent", npb.config("tca", **persist), 5),
                 ("nodp_cta_tiles_no_launch_code", npb.config("nodp", granularity="none", **chunk), 5),
                 ("cdp_threshold_above_max_degree", npb.config("cdp", threshold=npb.INT32_MAX, **chunk), 5),
                 ("plain_cdp", npb.config("cdp"), cdp_steps),
                 ("t_c", npb.config("tc"), cdp_steps)]
+    graph_only = [] if workload == "bt64k" else [
+        ("t_c_a_persistent", npb.config("tca", driver=npb.NP_DRIVER_PERSISTENT), 5),
+        ("nodp_persistent", npb.config("nodp", driver=npb.NP_DRIVER_PERSISTENT), 5)]
     return [("plain_cdp", npb.config("cdp"), cdp_steps), ("nodp", npb.config("nodp"), cdp_steps),
             ("t_c", npb.config("tc"), cdp_steps),
             ("t_c_a_multiblock", npb.config("tca", granularity="multiblock", group_blocks=8), 5),
             ("t_c_a_grid_device", npb.config("tca", granularity="grid_device"), 5),
-            ("t_c_a_block", npb.config("tca", granularity="block"), 5)]
+            ("t_c_a_block", npb.config("tca", granularity="block"), 5)] + graph_only
 
 
 def run_ours(args, ws, rank, local):

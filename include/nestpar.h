@@ -84,6 +84,10 @@ typedef int32_t np_status;
 #define NP_DRIVER_HOST 1      /* host loop: one level per launch, count read back after each (the paper's form) */
 #define NP_DRIVER_CHUNK 2     /* host-replayed CUDA graph of `unroll` levels, count read back after each chunk */
 #define NP_DRIVER_WHILE 3     /* conditional-while CUDA graph (NODP and GRID_HOST only) */
+#define NP_DRIVER_PERSISTENT 4 /* one cooperative kernel runs every level (NODP and GRID_HOST only):
+                                  the parent phase, a grid barrier, the aggregated child phase and a
+                                  grid barrier per level, in place of kernel boundaries; barrier waits
+                                  are bounded (5 s, then NP_ERR_TIMEOUT) */
 
 typedef struct np_config {
   int32_t variant;       /* NP_VARIANT_* */

@@ -81,6 +81,8 @@ struct __align__(16) LevelState {
   unsigned long long s[S_N];     // counters (np_stats)
   int body_iters;                // conditional-while iterations of this solve (bounded)
   int pad;
+  unsigned bar_count;            // grid barrier of the persistent level loop: arrivals
+  unsigned bar_gen;              // and generation
 };
 
 __device__ __forceinline__ unsigned long long level_epoch(const LevelState* st, int L) {
@@ -672,38 +674,19 @@ __global__ void NP_CHILD_BOUNDS child_direct(BodyArgs b, int pid, int base, int 
   run_coarsened<Body, CF>(b, p, N, blockIdx.x, blockDim.x, threadIdx.x, sink);
 }
 
-// Aggregated child grid: disaggregation + coarsened body. A CTA hosts
-// blockDim.x / cb child blocks of cb threads that run independently (no CTA
-// barrier on this path). When launched with fewer child blocks than
-// aggregated blocks (the grid-host form, whose size is read from device
-// memory) each child block takes a contiguous range of aggregated blocks, so
-// after the first search the parent index only moves forward.
+// Aggregated child blocks [0, total) of the records rec[0, nrec) with block
+// offsets boff: disaggregation + coarsened body. A CTA hosts blockDim.x / cb
+// child blocks of cb threads that run independently (no CTA barrier on this
+// path). With fewer child blocks than aggregated blocks (the persistent
+// grid-host forms, whose size is fixed before the total is known) each child
+// block takes a contiguous range of aggregated blocks, so after the first
+// search the parent index only moves forward.
 template <class Body, int CF>
-__global__ void NP_CHILD_BOUNDS child_agg(BodyArgs b, AggSeg s) {
-  __shared__ int s_stage[kCtaStage];
-  __shared__ int s_stage_n, s_stage_base;
-  if (threadIdx.x == 0) s_stage_n = 0;
-  int nrec = s.nrec, total = s.total;
-  LevelState* st = b.st;
-  if (s.mode != 0) {
-    int L = b.L;
-    if (s.level_mode) {
-      L = __ldcg(&st->base) + s.k;
-      b.L = L;
-      b.next = (L & 1) ? s.fr0 : s.fr1;
-      b.next_count = &st->count[(L + 1) % 3];
-    }
-    const int slot = L & 3;
-    if (s.mode == 1) {
-      nrec = __ldcg(&st->agg_records[slot]);
-      total = __ldcg(&st->agg_blocks[slot]);
-    } else {
-      const unsigned long long acc = __ldcg(&st->agg_acc[slot]);
-      nrec = (int)(acc >> 40);
-      total = (int)(acc & ((1ull << 40) - 1));
-    }
-  }
-  const int cb = s.cb, per_cta = (int)blockDim.x / cb;
+__device__ __forceinline__ void child_agg_run(const BodyArgs& b, const int4* rec, const int* boff, int nrec,
+                                              int total, int cb, bool count_blocks, int* s_stage, int* s_stage_n,
+                                              int* s_stage_base) {
+  if (threadIdx.x == 0) *s_stage_n = 0;
+  const int per_cta = (int)blockDim.x / cb;
   const int sub = (int)blockIdx.x * per_cta + (int)threadIdx.x / cb, stid = (int)threadIdx.x % cb;
   const int chunk = ceil_div(total, (int)gridDim.x * per_cta);
   const int first = sub * chunk;
@@ -711,22 +694,56 @@ __global__ void NP_CHILD_BOUNDS child_agg(BodyArgs b, AggSeg s) {
   int j = -1, next_off = 0, off = 0, N = 0;
   typename Body::P p{};
   __syncthreads();
-  StageSink sink{b.next, b.next_count, s_stage, &s_stage_n};
+  StageSink sink{b.next, b.next_count, s_stage, s_stage_n};
   for (int B0 = first; B0 < last; B0++) {
     if (j < 0 || B0 >= next_off) {
-      j = j < 0 ? warp_search(s.boff, 0, nrec, B0) : warp_search_near(s.boff, j + 1, nrec, B0);
-      const int4 r = __ldcg(&s.rec[j]);
-      off = __ldcg(&s.boff[j]);
-      next_off = j + 1 < nrec ? __ldcg(&s.boff[j + 1]) : 0x7fffffff;
+      j = j < 0 ? warp_search(boff, 0, nrec, B0) : warp_search_near(boff, j + 1, nrec, B0);
+      const int4 r = __ldcg(&rec[j]);
+      off = __ldcg(&boff[j]);
+      next_off = j + 1 < nrec ? __ldcg(&boff[j + 1]) : 0x7fffffff;
       N = r.z;
       p = Body::parent(b, r.x, r.y, r.z);
     }
     run_coarsened<Body, CF>(b, p, N, B0 - off, cb, stid, sink);
   }
-  if constexpr (Body::kPushes) stage_flush(s_stage, &s_stage_n, b.next, b.next_count, &s_stage_base);
-  // persistent (grid-host) form: count its blocks here; device-launched
+  if constexpr (Body::kPushes) stage_flush(s_stage, s_stage_n, b.next, b.next_count, s_stage_base);
+  // persistent (grid-host) forms count their blocks here; device-launched
   // grids are counted by the launching parent
-  if (s.mode != 0 && stid == 0 && last > first) add_stat(st, S_CBLOCKS, (unsigned long long)(last - first));
+  if (count_blocks && stid == 0 && last > first) add_stat(b.st, S_CBLOCKS, (unsigned long long)(last - first));
+}
+
+// Totals of the grid-host aggregation of level L (look-back or atomic scan).
+__device__ __forceinline__ void agg_totals(const LevelState* st, int L, int mode, int& nrec, int& total) {
+  const int slot = L & 3;
+  if (mode == 1) {
+    nrec = __ldcg(&st->agg_records[slot]);
+    total = __ldcg(&st->agg_blocks[slot]);
+  } else {
+    const unsigned long long acc = __ldcg(&st->agg_acc[slot]);
+    nrec = (int)(acc >> 40);
+    total = (int)(acc & ((1ull << 40) - 1));
+  }
+}
+
+// Aggregated child grid: a device-launched grid over one segment (mode 0), or
+// the stream-ordered persistent grid of the grid-host form, whose level and
+// totals are read from the level state.
+template <class Body, int CF>
+__global__ void NP_CHILD_BOUNDS child_agg(BodyArgs b, AggSeg s) {
+  __shared__ int s_stage[kCtaStage];
+  __shared__ int s_stage_n, s_stage_base;
+  int nrec = s.nrec, total = s.total;
+  if (s.mode != 0) {
+    int L = b.L;
+    if (s.level_mode) {
+      L = __ldcg(&b.st->base) + s.k;
+      b.L = L;
+      b.next = (L & 1) ? s.fr0 : s.fr1;
+      b.next_count = &b.st->count[(L + 1) % 3];
+    }
+    agg_totals(b.st, L, s.mode, nrec, total);
+  }
+  child_agg_run<Body, CF>(b, s.rec, s.boff, nrec, total, s.cb, s.mode != 0, s_stage, &s_stage_n, &s_stage_base);
 }
 
 // --------------------------------------------------------------- parent side
@@ -972,21 +989,15 @@ __global__ void NP_PARENT_BOUNDS parent_kernel(Args a) {
 // loop (lanes with fewer children idle) that appends through a warp sink. No
 // CTA barrier anywhere, so no warp waits for another warp's serial loop.
 template <class Body, int FORM>
-__global__ void NP_PARENT_BOUNDS parent_warp(Args a) {
-  __shared__ int s_stage[kCtaStage];
-  __shared__ int s_stage_n, s_stage_base;
+__device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count, bool fixed, int* s_stage,
+                                                int* s_stage_n, int* s_stage_base) {
   const int lane = threadIdx.x & 31;
   LevelState* st = a.st;
-  const bool fixed = a.count_fixed >= 0;
-  int L = a.L_fixed, count = a.count_fixed;
-  if (!fixed) level_of(st, a.k, L, count);
   const int slot = L & 3;
-  if (!fixed && blockIdx.x == 0 && threadIdx.x == 0) level_open(st, L, count);
-  if (count <= 0) return;   // uniform over the grid
   const int ntiles = ceil_div(count, 32);
   // CTAs whose warps would all find no tile leave at once
   if ((int)blockIdx.x * ((int)blockDim.x >> 5) >= ntiles) return;
-  if (threadIdx.x == 0) s_stage_n = 0;
+  if (threadIdx.x == 0) *s_stage_n = 0;
   __syncthreads();
   const unsigned long long epoch = level_epoch(st, L);
   const int* ids = fixed ? a.ids : ((L & 1) ? a.fr1 : a.fr0);
@@ -996,7 +1007,7 @@ __global__ void NP_PARENT_BOUNDS parent_warp(Args a) {
   b.next_count = fixed ? a.next_count_ovr : &st->count[(L + 1) % 3];
   const int T = a.threshold < 1 ? 1 : a.threshold;
   const int CB = a.child_block;
-  StageSink sink{b.next, b.next_count, s_stage, &s_stage_n};
+  StageSink sink{b.next, b.next_count, s_stage, s_stage_n};
   unsigned long long n_par = 0, n_items = 0, n_serial = 0, n_launch = 0, n_citems = 0;
 
   for (;;) {
@@ -1087,7 +1098,7 @@ __global__ void NP_PARENT_BOUNDS parent_warp(Args a) {
       }
     }
   }
-  if constexpr (Body::kPushes) stage_flush(s_stage, &s_stage_n, b.next, b.next_count, &s_stage_base);
+  if constexpr (Body::kPushes) stage_flush(s_stage, s_stage_n, b.next, b.next_count, s_stage_base);
   if (lane == 0) {
     add_stat(st, S_PARENTS, n_par);
     add_stat(st, S_ITEMS, n_items);
@@ -1095,6 +1106,106 @@ __global__ void NP_PARENT_BOUNDS parent_warp(Args a) {
     add_stat(st, S_LAUNCHP, n_launch);
     add_stat(st, S_CITEMS, n_citems);
   }
+}
+
+template <class Body, int FORM>
+__global__ void NP_PARENT_BOUNDS parent_warp(Args a) {
+  __shared__ int s_stage[kCtaStage];
+  __shared__ int s_stage_n, s_stage_base;
+  LevelState* st = a.st;
+  const bool fixed = a.count_fixed >= 0;
+  int L = a.L_fixed, count = a.count_fixed;
+  if (!fixed) level_of(st, a.k, L, count);
+  if (!fixed && blockIdx.x == 0 && threadIdx.x == 0) level_open(st, L, count);
+  if (count <= 0) return;   // uniform over the grid
+  parent_warp_run<Body, FORM>(a, L, count, fixed, s_stage, &s_stage_n, &s_stage_base);
+}
+
+// ------------------------------------------------- persistent level loop
+//
+// The whole level loop of a form without device launches in one cooperative
+// kernel (all CTAs co-resident): per level the warp-tiled parent phase, then
+// (grid aggregation) a grid barrier and the aggregated child phase over the
+// same CTAs, then a grid barrier before the next level. The barriers stand in
+// for the kernel boundaries of the graph drivers; the level state, frontiers
+// and records are the same. Every wait is bounded in time: a barrier that
+// does not complete within kBarrierNs sets the timeout bit and every CTA
+// leaves the loop.
+constexpr unsigned long long kBarrierNs = 5000000000ull;   // 5 s
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Returns false (in every thread of the CTA) once any CTA has timed out.
+__device__ __forceinline__ bool grid_barrier(LevelState* st, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    const unsigned gen = ld_acquire_u32(&st->bar_gen);
+    __threadfence();
+    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+      st->bar_count = 0u;
+      __threadfence();
+      st_release_u32(&st->bar_gen, gen + 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      unsigned polls = 0;
+      while (ld_acquire_u32(&st->bar_gen) == gen) {
+        if ((++polls & 63u) == 0u) {
+          if (globaltimer_ns() - t0 > kBarrierNs || (__ldcg(&st->error) & kErrTimeout)) {
+            atomicOr(&st->error, kErrTimeout);
+            ok = false;
+            break;
+          }
+        }
+        __nanosleep(64);
+      }
+    }
+    *s_ok = ok && !(__ldcg(&st->error) & kErrTimeout);
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+template <class Body, int FORM, int CF>
+__global__ void __launch_bounds__(1024) level_loop(Args a, int max_levels) {
+  __shared__ int s_stage[kCtaStage];
+  __shared__ int s_stage_n, s_stage_base, s_ok;
+  LevelState* st = a.st;
+  int L = __ldcg(&st->base);
+  while (L < max_levels) {
+    const int count = __ldcg(&st->count[L % 3]);
+    if (count <= 0) break;   // uniform: every CTA reads it after the same barrier
+    if (blockIdx.x == 0 && threadIdx.x == 0) level_open(st, L, count);
+    parent_warp_run<Body, FORM>(a, L, count, false, s_stage, &s_stage_n, &s_stage_base);
+    if constexpr (FORM == 1) {
+      if (!grid_barrier(st, &s_ok)) break;
+      BodyArgs b = a.b;
+      b.L = L;
+      b.next = (L & 1) ? a.fr0 : a.fr1;
+      b.next_count = &st->count[(L + 1) % 3];
+      int nrec = 0, total = 0;
+      agg_totals(st, L, a.scan == 0 ? 1 : 2, nrec, total);
+      child_agg_run<Body, CF>(b, a.rec, a.boff, nrec, total, a.child_block, true, s_stage, &s_stage_n,
+                              &s_stage_base);
+    }
+    if (!grid_barrier(st, &s_ok)) break;
+    L++;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->base = L;
 }
 
 }  // namespace nestpar

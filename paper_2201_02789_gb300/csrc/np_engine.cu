@@ -41,6 +41,7 @@ __device__ __forceinline__ void reset_slots(LevelState* st) {
   }
   for (int k = 0; k < S_N; k++) st->s[k] = 0ull;
   st->body_iters = 0;
+  st->bar_count = 0u;
   st->solve_id += 1;
 }
 
@@ -248,7 +249,7 @@ np_status check_config(const np_config* cfg) {
   if (cfg->child_block < 32 || cfg->child_block > 1024 || cfg->child_block % 32) return NP_ERR_INVALID;
   if (cfg->parent_block < 64 || cfg->parent_block > kMaxParentBlock || cfg->parent_block % 32) return NP_ERR_INVALID;
   if (cfg->scan != NP_SCAN_LOOKBACK && cfg->scan != NP_SCAN_ATOMIC) return NP_ERR_INVALID;
-  if (cfg->driver < NP_DRIVER_AUTO || cfg->driver > NP_DRIVER_WHILE) return NP_ERR_INVALID;
+  if (cfg->driver < NP_DRIVER_AUTO || cfg->driver > NP_DRIVER_PERSISTENT) return NP_ERR_INVALID;
   if (cfg->unroll < 1 || cfg->unroll > 16) return NP_ERR_INVALID;
   if (cfg->parent_grid < 0) return NP_ERR_INVALID;
   for (int k = 0; k < 4; k++)
@@ -263,11 +264,13 @@ Plan make_plan(const BodyKernels& K, const np_config& cfg) {
     // warp tiles; with granularity NONE the CTA-tiled kernel of the
     // device-launch forms without its launch code (dead-launch-code baseline)
     p.parent = cfg.granularity == NP_GRAN_NONE ? K.parent_nodp_cta : K.parent_nodp;
+    p.loop = cfg.granularity == NP_GRAN_NONE ? nullptr : K.level_loop_nodp;
     p.mode = M_NODP;
     p.gran = G_NODP;
   } else if (cfg.granularity == NP_GRAN_GRID_HOST) {
     p.parent = K.parent_grid_host;
     p.child = K.child_agg[cfi];
+    p.loop = K.level_loop_agg[cfi];
     p.mode = M_GRID_HOST;
     p.gran = G_GRID_HOST;
   } else {
@@ -564,11 +567,31 @@ np_status finish(Engine& e, const Workspace& w, cudaStream_t s, np_stats* stats)
   return status_from_bits(h.error);
 }
 
+np_status launch_level_loop(Engine& e, const Plan& p, const Args& a, const np_config& cfg, int max_levels,
+                            cudaStream_t s) {
+  // one block size for both phases: a multiple of 32 (parent warps) and of the
+  // child block (child sub-blocks), at least the parent block and 256
+  const int cb = cfg.child_block;
+  int blk = cfg.parent_block > 256 ? cfg.parent_block : 256;
+  if (blk < cb) blk = cb;
+  blk = (blk + cb - 1) / cb * cb;
+  if (blk > 1024) return NP_ERR_UNSUPPORTED;
+  const int grid = occupancy(e, p.loop, blk) * e.sms;
+  Args aa = a;
+  aa.k = 0;
+  int ml = max_levels;
+  void* args[] = {&aa, &ml};
+  NP_CK(cudaLaunchCooperativeKernel(p.loop, dim3(grid), dim3(blk), args, 0, s));
+  return NP_OK;
+}
+
 np_status run_levels(Engine& e, Workspace& w, const Plan& p, const Args& a, const np_config& cfg, int64_t parents,
                      int max_levels, cudaStream_t s) {
   Grids g = grids_for(e, p, cfg, parents);
   const int driver = resolve_driver(p, cfg);
-  if (driver == NP_DRIVER_WHILE && p.mode == M_DEVICE_LAUNCH) return NP_ERR_UNSUPPORTED;
+  if ((driver == NP_DRIVER_WHILE || driver == NP_DRIVER_PERSISTENT) && p.mode == M_DEVICE_LAUNCH)
+    return NP_ERR_UNSUPPORTED;
+  if (driver == NP_DRIVER_PERSISTENT && !p.loop) return NP_ERR_UNSUPPORTED;
   if (e.profile) {
     // per-level records describe this call only
     e.prof.levels = 0;
@@ -589,6 +612,7 @@ np_status run_levels(Engine& e, Workspace& w, const Plan& p, const Args& a, cons
     NP_CK(cudaGraphLaunch(exec, s));
     return NP_OK;
   }
+  if (driver == NP_DRIVER_PERSISTENT) return launch_level_loop(e, p, a, cfg, max_levels, s);
   cudaGraphExec_t exec = nullptr;
   if (driver == NP_DRIVER_CHUNK) NP_TRY(chunk_graph(e, w, p, a, g, cfg.unroll, &exec));
   for (int iter = 0;; iter++) {

@@ -50,6 +50,7 @@ enum Mode : int { M_NODP = 0, M_GRID_HOST = 1, M_DEVICE_LAUNCH = 2 };
 struct Plan {
   const void* parent = nullptr;
   const void* child = nullptr;  // persistent child grid (grid-host form)
+  const void* loop = nullptr;   // persistent level loop (NODP and grid-host forms)
   int mode = M_NODP;
   int gran = G_NODP;
 };
@@ -138,6 +139,9 @@ np_status finish(Engine& e, const Workspace& w, cudaStream_t s, np_stats* stats)
 np_status run_levels(Engine& e, Workspace& w, const Plan& p, const Args& a, const np_config& cfg, int64_t parents,
                      int max_levels, cudaStream_t s);
 np_status check_csr(const np_csr* g, bool need_w);
+// The persistent level loop (NP_DRIVER_PERSISTENT) as one cooperative launch on s.
+np_status launch_level_loop(Engine& e, const Plan& p, const Args& a, const np_config& cfg, int max_levels,
+                            cudaStream_t s);
 
 // ---- device-side initialisation kernels (np_engine.cu)
 __global__ void init_solve_kernel(LevelState* st, int kind, int n, int src, int* level, unsigned* dist, int* stamp,

@@ -22,6 +22,8 @@ struct BodyKernels {
   const void* parent[4][kNumCF];              // [NONE, WARP, BLOCK, MULTIBLOCK/GRID_DEVICE][cf]
   const void* child_direct[kNumCF];
   const void* child_agg[kNumCF];
+  const void* level_loop_nodp;                // level_loop<Body, 0, 1>: persistent no-DP level loop
+  const void* level_loop_agg[kNumCF];         // level_loop<Body, 1, cf>: persistent grid-aggregation loop
 };
 
 const BodyKernels& bfs_kernels();

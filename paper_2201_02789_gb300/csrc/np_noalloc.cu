@@ -53,6 +53,7 @@ DeviceScratch g_devices[kMaxDevices];
 __global__ void noalloc_reset_kernel(LevelState* st) {
   st->solve_id += 1;
   st->body_iters = 0;
+  st->bar_count = 0u;
   for (int k = 0; k < 4; k++) {
     st->ticket[k] = 0;
     st->agg_records[k] = 0;

@@ -39,7 +39,6 @@ struct __align__(16) Ctl {
 };
 
 size_t ctl_bytes(int S) { return sizeof(Ctl) + sizeof(int4) * (size_t)S + sizeof(int) * (size_t)S; }
-const int4* ctl_adm(const Ctl* c) { return reinterpret_cast<const int4*>(c + 1); }
 int4* ctl_adm(Ctl* c) { return reinterpret_cast<int4*>(c + 1); }
 
 __device__ __forceinline__ const int4* dctl_adm(const Ctl* c) { return reinterpret_cast<const int4*>(c + 1); }

@@ -34,6 +34,12 @@ inline BodyKernels make_table() {
   t.child_agg[2] = (const void*)child_agg<Body, 4>;
   t.child_agg[3] = (const void*)child_agg<Body, 8>;
   t.child_agg[4] = (const void*)child_agg<Body, 16>;
+  t.level_loop_nodp = (const void*)level_loop<Body, 0, 1>;
+  t.level_loop_agg[0] = (const void*)level_loop<Body, 1, 1>;
+  t.level_loop_agg[1] = (const void*)level_loop<Body, 1, 2>;
+  t.level_loop_agg[2] = (const void*)level_loop<Body, 1, 4>;
+  t.level_loop_agg[3] = (const void*)level_loop<Body, 1, 8>;
+  t.level_loop_agg[4] = (const void*)level_loop<Body, 1, 16>;
   return t;
 }
 

@@ -23,7 +23,7 @@ NP_OK, NP_ERR_INVALID, NP_ERR_CUDA, NP_ERR_NOMEM, NP_ERR_CAPACITY, NP_ERR_LAUNCH
 NP_VARIANT_NODP, NP_VARIANT_CDP = 0, 1
 NP_GRAN_NONE, NP_GRAN_WARP, NP_GRAN_BLOCK, NP_GRAN_MULTIBLOCK, NP_GRAN_GRID_DEVICE, NP_GRAN_GRID_HOST = range(6)
 NP_SCAN_LOOKBACK, NP_SCAN_ATOMIC = 0, 1
-NP_DRIVER_AUTO, NP_DRIVER_HOST, NP_DRIVER_CHUNK, NP_DRIVER_WHILE = range(4)
+NP_DRIVER_AUTO, NP_DRIVER_HOST, NP_DRIVER_CHUNK, NP_DRIVER_WHILE, NP_DRIVER_PERSISTENT = range(5)
 NP_COUNT_CSR_DEGREE, NP_COUNT_BEZIER = 0, 1
 NP_BODY_BFS_VISIT, NP_BODY_SSSP_RELAX, NP_BODY_BEZIER_EVAL = 0, 1, 2
 NP_BATCH_BFS, NP_BATCH_SSSP = 0, 1

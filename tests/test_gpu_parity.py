@@ -77,6 +77,16 @@ EXTRA = [
     ("driver-while1", dict(driver=npb.NP_DRIVER_WHILE, unroll=1)),
     ("driver-while16", dict(driver=npb.NP_DRIVER_WHILE, unroll=16, threshold=0)),
     ("nodp-host", dict(variant=npb.NP_VARIANT_NODP, driver=npb.NP_DRIVER_HOST)),
+    ("persistent", dict(driver=npb.NP_DRIVER_PERSISTENT)),
+    ("persistent-T1-C1", dict(driver=npb.NP_DRIVER_PERSISTENT, threshold=1, cfactor=1)),
+    ("persistent-T0-C16", dict(driver=npb.NP_DRIVER_PERSISTENT, threshold=0, cfactor=16)),
+    ("persistent-lb", dict(driver=npb.NP_DRIVER_PERSISTENT, scan=npb.NP_SCAN_LOOKBACK, threshold=4)),
+    ("persistent-cb1024", dict(driver=npb.NP_DRIVER_PERSISTENT, child_block=1024, threshold=1)),
+    ("persistent-pb512-cb128", dict(driver=npb.NP_DRIVER_PERSISTENT, parent_block=512, child_block=128,
+                                    threshold=2)),
+    ("persistent-pb384-cb256", dict(driver=npb.NP_DRIVER_PERSISTENT, parent_block=384, child_block=256,
+                                    threshold=2)),
+    ("persistent-nodp", dict(variant=npb.NP_VARIANT_NODP, driver=npb.NP_DRIVER_PERSISTENT)),
 ]
 
 
@@ -91,11 +101,17 @@ def test_extra_settings_bitexact(ctx, g4k, name, kw):
     assert st["error"] == 0 and st2["error"] == 0
 
 
-def test_while_driver_refuses_device_launch_forms(ctx, g4k):
+@pytest.mark.parametrize("driver", [npb.NP_DRIVER_WHILE, npb.NP_DRIVER_PERSISTENT])
+def test_graph_drivers_refuse_device_launch_forms(ctx, g4k, driver):
     _, dg, _, _ = g4k
-    cfg = npb.config("tca", granularity="block", driver=npb.NP_DRIVER_WHILE)
     level = torch.empty(dg.n, dtype=torch.int32, device="cuda:0")
-    assert npb.np_bfs(ctx.handle, dg.csr, 0, level, cfg, check=False) == npb.NP_ERR_UNSUPPORTED
+    for gran in ("none", "block", "multiblock", "grid_device"):
+        cfg = npb.config("tca", granularity=gran, driver=driver)
+        assert npb.np_bfs(ctx.handle, dg.csr, 0, level, cfg, check=False) == npb.NP_ERR_UNSUPPORTED
+    # the dead-launch-code baseline (NODP, CTA tiles) has no persistent loop either
+    if driver == npb.NP_DRIVER_PERSISTENT:
+        cfg = npb.config("nodp", granularity="none", driver=driver)
+        assert npb.np_bfs(ctx.handle, dg.csr, 0, level, cfg, check=False) == npb.NP_ERR_UNSUPPORTED
 
 
 # ------------------------------------------------------------------ edge cases
@@ -128,12 +144,15 @@ EDGE = _edge_graphs()
 
 
 @pytest.mark.parametrize("gname", list(EDGE))
-@pytest.mark.parametrize("form", ["nodp", "cdp", "tc", "tca", "mb", "block"])
+@pytest.mark.parametrize("form", ["nodp", "cdp", "tc", "tca", "mb", "block", "persist", "persist-nodp"])
 def test_edge_graphs(ctx, gname, form):
     g = EDGE[gname]
     kw = {"mb": dict(granularity="multiblock", group_blocks=2, threshold=4),
-          "block": dict(granularity="block", threshold=1, cfactor=2)}.get(form, {})
-    cfg = npb.config(form if form in ("nodp", "cdp", "tc", "tca") else "tca", **kw)
+          "block": dict(granularity="block", threshold=1, cfactor=2),
+          "persist": dict(driver=npb.NP_DRIVER_PERSISTENT, threshold=2),
+          "persist-nodp": dict(driver=npb.NP_DRIVER_PERSISTENT)}.get(form, {})
+    base = {"persist": "tca", "persist-nodp": "nodp"}.get(form, form)
+    cfg = npb.config(base if base in ("nodp", "cdp", "tc", "tca") else "tca", **kw)
     dg = DevGraph(g)
     for src in sorted({0, g.n - 1, g.n // 2}):
         np.testing.assert_array_equal(bfs(ctx, dg, src, cfg), oracle.bfs(g.row_ptr, g.col, src))
@@ -305,11 +324,13 @@ def rmat20():
     return g, DevGraph(g)
 
 
-@pytest.mark.parametrize("form", ["tca", "nodp", "tca-mb", "tca-atomic"])
+@pytest.mark.parametrize("form", ["tca", "nodp", "tca-mb", "tca-atomic", "tca-persistent", "nodp-persistent"])
 def test_rmat20_sssp_bfs_full(ctx, rmat20, form):
     g, dg = rmat20
     kw = {"tca-mb": dict(granularity="multiblock", group_blocks=8),
-          "tca-atomic": dict(scan=npb.NP_SCAN_ATOMIC)}.get(form, {})
+          "tca-atomic": dict(scan=npb.NP_SCAN_ATOMIC),
+          "tca-persistent": dict(driver=npb.NP_DRIVER_PERSISTENT),
+          "nodp-persistent": dict(driver=npb.NP_DRIVER_PERSISTENT)}.get(form, {})
     cfg = npb.config(form.split("-")[0], **kw)
     ref_l = oracle.bfs(g.row_ptr, g.col, 0)
     np.testing.assert_array_equal(bfs(ctx, dg, 0, cfg), ref_l)
