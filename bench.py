@@ -584,7 +584,7 @@ def run_ours(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if wl["kind"] == "bezier" else "u32", "data": "synthetic",
             "config": dict(wl["config"], l2=L2_NOTE),
-            "form": "threshold 32 + coarsening 8 (32-thread child blocks) + grid aggregation (atomic scan), "
+            "form": "threshold 32 + coarsening 4 (64-thread child blocks) + grid aggregation (atomic scan), "
                     "while-graph level loop",
             "ms_per_solve": {"median": statistics.median(ms), "min": min(ms)},
             "units_per_solve": units, "levels": st["levels"], "child_items": st["items"],

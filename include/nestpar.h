@@ -107,8 +107,8 @@ typedef struct np_config {
   int32_t reserved[4];   /* must be zero */
 } np_config;
 
-/* Fills the library defaults: CDP, threshold 32, cfactor 8, grid-host
- * aggregation, atomic scan, child block 32, parent block 256, AUTO driver
+/* Fills the library defaults: CDP, threshold 32, cfactor 4, grid-host
+ * aggregation, atomic scan, child block 64, parent block 256, AUTO driver
  * (the best of a threshold x cfactor x child-block x scan sweep of BFS and SSSP
  * on an R-MAT scale-20 graph on GB300; the look-back scan, which keeps records
  * in parent order, is selectable and slower there because it publishes and

@@ -189,11 +189,11 @@ np_status np_config_default(np_config* cfg) {
   std::memset(cfg, 0, sizeof(*cfg));
   cfg->variant = NP_VARIANT_CDP;
   cfg->threshold = 32;
-  cfg->cfactor = 8;
+  cfg->cfactor = 4;
   cfg->granularity = NP_GRAN_GRID_HOST;
   cfg->group_blocks = 8;
   cfg->agg_threshold = 0;
-  cfg->child_block = 32;
+  cfg->child_block = 64;
   cfg->parent_block = 256;
   cfg->scan = NP_SCAN_ATOMIC;
   cfg->driver = NP_DRIVER_AUTO;

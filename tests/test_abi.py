@@ -89,8 +89,8 @@ def test_host_only_entry_points(lib):
     assert npb.np_version() == 10100
     assert npb.np_status_string(npb.NP_ERR_INVALID) == "invalid argument"
     cfg = npb.np_config_default()
-    assert (cfg.variant, cfg.threshold, cfg.cfactor, cfg.granularity, cfg.scan) == (1, 32, 8, npb.NP_GRAN_GRID_HOST, npb.NP_SCAN_ATOMIC)
-    assert cfg.child_block == 32
+    assert (cfg.variant, cfg.threshold, cfg.cfactor, cfg.granularity, cfg.scan) == (1, 32, 4, npb.NP_GRAN_GRID_HOST, npb.NP_SCAN_ATOMIC)
+    assert cfg.child_block == 64
     assert npb.np_workspace_size(1 << 20, cfg) > (1 << 20) * 16
     with pytest.raises(npb.NestparError):
         npb.np_workspace_size(-1, cfg)
