@@ -82,7 +82,10 @@ typedef int32_t np_status;
 
 #define NP_DRIVER_AUTO 0      /* conditional-while CUDA graph when no device launch is needed, else host-replayed graph chunks */
 #define NP_DRIVER_HOST 1      /* host loop: one level per launch, count read back after each (the paper's form) */
-#define NP_DRIVER_CHUNK 2     /* host-replayed CUDA graph of `unroll` levels, count read back after each chunk */
+#define NP_DRIVER_CHUNK 2     /* `unroll` levels per host round trip, count read back after each chunk: a
+                                 replayed CUDA graph for NODP / GRID_HOST, direct stream launches for
+                                 the device-launch forms (a graph kernel node does not wait for the
+                                 grids it launches from the device; a stream-launched kernel does) */
 #define NP_DRIVER_WHILE 3     /* conditional-while CUDA graph (NODP and GRID_HOST only) */
 #define NP_DRIVER_PERSISTENT 4 /* one cooperative kernel runs every level (NODP and GRID_HOST only):
                                   the parent phase, a grid barrier, the aggregated child phase and a
@@ -318,6 +321,18 @@ np_status np_bezier(np_ctx *ctx, const float *ctrl, int32_t ncurves, int32_t *of
                     float *points, int64_t cap, const np_config *cfg, void *stream,
                     np_stats *stats);
 
+/* Triangle counting, the second CSR workload on the same engine (Section VII's
+ * nested-parallel pattern with an adjacency-intersection child). `dag` is an
+ * acyclic orientation of a simple undirected graph: every undirected edge
+ * appears once, from one endpoint to the other, with sorted out-lists N+ and
+ * no self-loops or duplicates. Parent = vertex u, N = |N+(u)|, child item =
+ * out-edge u -> v, which counts the w in both N+(u) and N+(v) (the shorter
+ * list is walked, the longer binary-searched). *count (device uint64)
+ * receives the number of triangles. Every form (NODP, plain CDP, T, C, A at
+ * every granularity) runs one pass over the n parents. */
+np_status np_triangles(np_ctx *ctx, const np_csr *dag, uint64_t *count, const np_config *cfg,
+                       void *stream, np_stats *stats);
+
 /* ---- allocation-free tessellation (the paper has no counterpart) ----
  * Some callers cannot allocate device memory at the time they call this
  * library: code recording its GPU work into a CUDA graph by stream capture
@@ -354,6 +369,7 @@ np_status np_bezier_noalloc(const float *ctrl, int32_t ncurves, int32_t *offsets
 #define NP_BODY_BFS_VISIT 0     /* claim col[e] with level next_level, append it to `next` */
 #define NP_BODY_SSSP_RELAX 1    /* atomic-min relax col[e]; append improved targets once per `iteration` */
 #define NP_BODY_BEZIER_EVAL 2   /* write point i of curve p at points[offsets-scan + i] */
+#define NP_BODY_TRIANGLES 3     /* count |N+(p) cap N+(col[e])| into tri_counts (CSR count) */
 
 typedef struct np_parents {
   const int32_t *ids;     /* device [count] parent ids, or NULL for ids 0..count-1 */
@@ -374,7 +390,9 @@ typedef struct np_body {
   int32_t *offsets;       /* Bezier: [count + 1] device, written (exclusive scan in parent order) */
   float *points;          /* Bezier: [cap][2] device */
   int64_t cap;            /* Bezier: capacity of points in points */
+  uint64_t *tri_counts;   /* triangles: [NP_TRI_SLOTS] device partial counts, added to */
 } np_body;
+#define NP_TRI_SLOTS 256
 
 /* Runs the children of every parent once, in the form `cfg` selects. For CSR
  * counts `g` describes the graph; for Bezier counts `g` may be NULL. */

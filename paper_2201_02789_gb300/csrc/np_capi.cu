@@ -19,6 +19,7 @@ struct np_ctx {
   Workspace w;
   int* ids = nullptr;                 // device copy of the sources of a multi-source solve
   int ids_cap = 0;
+  unsigned long long* tri = nullptr;  // triangle-counting partial sums [kTcSlots]
   // device staging for the *_host entry points
   unsigned char* stage = nullptr;
   size_t stage_bytes = 0;
@@ -141,6 +142,13 @@ np_status fixed_pass(np_ctx* c, const Args& a0, const np_config& cfg, const Body
     c->e.prof.other_launches += 1;
     return profiled_pass(c->e, c->w, p, a, g, false, s);
   }
+  if (p.mode == M_DEVICE_LAUNCH) {
+    // device launches are joined by stream order only (a graph node does not
+    // wait for the grids it launches): no graph for these forms
+    init_fixed_kernel<<<1, 1, 0, s>>>(c->w.st);
+    NP_CK(cudaGetLastError());
+    return enqueue_pass(p, a, g, false, 0, s);
+  }
   std::string key = graph_key("fixed", p, a, g, 1);
   auto it = c->w.graphs.find(key);
   cudaGraphExec_t exec = nullptr;
@@ -233,6 +241,7 @@ np_status np_destroy(np_ctx* c) {
   ws_release(c->w);
   if (c->stage) cudaFree(c->stage);
   if (c->ids) cudaFree(c->ids);
+  if (c->tri) cudaFree(c->tri);
   engine_release(c->e);
   delete c;
   return NP_OK;
@@ -261,6 +270,31 @@ np_status np_bfs(np_ctx* c, const np_csr* g, int32_t src, int32_t* level, const 
 np_status np_sssp(np_ctx* c, const np_csr* g, int32_t src, uint32_t* dist, const np_config* cfg, void* stream,
                   np_stats* stats) {
   return solve(c, 1, g, src, nullptr, dist, cfg, (cudaStream_t)stream, stats);
+}
+
+np_status np_triangles(np_ctx* c, const np_csr* dag, uint64_t* count, const np_config* cfg, void* stream,
+                       np_stats* stats) {
+  if (!c || !count) return NP_ERR_INVALID;
+  NP_TRY(check_config(cfg));
+  NP_TRY(check_csr(dag, false));
+  std::lock_guard<std::mutex> lk(c->mu);
+  NP_CK(cudaSetDevice(c->e.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!c->tri) NP_CK(cudaMalloc(&c->tri, sizeof(unsigned long long) * kTcSlots));
+  NP_TRY(ws_ensure(c->w, dag->n));
+  NP_CK(cudaMemsetAsync(c->tri, 0, sizeof(unsigned long long) * kTcSlots, s));
+  Args a;
+  base_args(c->w, *cfg, a);
+  a.count_fixed = dag->n;
+  a.L_fixed = 0;
+  a.row_ptr = dag->row_ptr;
+  a.b.col = dag->col_idx;
+  a.b.row_ptr = dag->row_ptr;
+  a.b.acc = c->tri;
+  NP_TRY(fixed_pass(c, a, *cfg, tc_kernels(), dag->n, s));
+  sum_u64_kernel<<<1, 256, 0, s>>>(c->tri, kTcSlots, reinterpret_cast<unsigned long long*>(count), 0);
+  NP_CK(cudaGetLastError());
+  return finish(c->e, c->w, s, stats);
 }
 
 np_status np_bfs_multi(np_ctx* c, const np_csr* g, int32_t nsrc, const int32_t* sources, int32_t* level, int64_t ld,
@@ -320,6 +354,11 @@ np_status np_run_nested(np_ctx* c, const np_parents* parents, int32_t count_kind
       if (!body->dist || !body->stamp || !body->next || !body->next_count || body->iteration < 1)
         return NP_ERR_INVALID;
       K = &sssp_kernels();
+    } else if (body->kind == NP_BODY_TRIANGLES) {
+      st = check_csr(g, false);
+      if (st != NP_OK) return st;
+      if (!body->tri_counts) return NP_ERR_INVALID;
+      K = &tc_kernels();
     } else {
       return NP_ERR_UNSUPPORTED;
     }
@@ -357,6 +396,10 @@ np_status np_run_nested(np_ctx* c, const np_parents* parents, int32_t count_kind
     a.L_fixed = body->iteration - 1;
     a.b.dist = body->dist;
     a.b.stamp = body->stamp;
+  } else if (body->kind == NP_BODY_TRIANGLES) {
+    a.L_fixed = 0;
+    a.b.row_ptr = g->row_ptr;
+    a.b.acc = reinterpret_cast<unsigned long long*>(body->tri_counts);
   } else {
     a.b.ctrl = body->ctrl;
     a.b.points = reinterpret_cast<float2*>(body->points);

@@ -6,10 +6,14 @@
 // Forms without a device launch site (NODP, grid-host aggregation) run the
 // whole loop inside a conditional-while CUDA graph: `unroll` levels per body
 // iteration, a one-thread kernel setting the condition, no host round trip.
-// Kernels containing device launches cannot sit in a conditional body, so the
-// device-launch forms replay a graph of `unroll` levels from the host and read
-// the frontier size back after each replay. NP_DRIVER_HOST is the paper's own
-// form: one host launch per level and a read-back after each.
+// The device-launch forms are never captured into a graph: measured on GB300
+// (CUDA 13.0, driver 580), a kernel node of a CUDA graph counts as complete
+// before the grids it launched from the device (fire-and-forget or tail
+// launch) have finished, so the next node could read a level or a result that
+// its children are still writing. A kernel launched on a stream does wait for
+// its children. So those forms enqueue `unroll` levels directly on the stream
+// and read the frontier size back after each chunk. NP_DRIVER_HOST is the
+// paper's own form: one host launch per level and a read-back after each.
 #include "np_engine.h"
 
 #include <climits>
@@ -113,6 +117,20 @@ __global__ void csr_check_kernel(const int* row_ptr, const int* col, int n, long
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) ok = ok && row_ptr[0] == 0 && (long long)row_ptr[n] == m;
   if (!ok) atomicOr(bad, 1);
+}
+
+__global__ void sum_u64_kernel(const unsigned long long* part, int n, unsigned long long* out, int accumulate) {
+  __shared__ unsigned long long s[32];
+  unsigned long long v = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; w++) t += s[w];
+    *out = accumulate ? *out + t : t;
+  }
 }
 
 // Between graph bodies or chunks: the next body position 0 is level base + K.
@@ -614,14 +632,15 @@ np_status run_levels(Engine& e, Workspace& w, const Plan& p, const Args& a, cons
   }
   if (driver == NP_DRIVER_PERSISTENT) return launch_level_loop(e, p, a, cfg, max_levels, s);
   cudaGraphExec_t exec = nullptr;
-  if (driver == NP_DRIVER_CHUNK) NP_TRY(chunk_graph(e, w, p, a, g, cfg.unroll, &exec));
+  if (driver == NP_DRIVER_CHUNK && p.mode != M_DEVICE_LAUNCH) NP_TRY(chunk_graph(e, w, p, a, g, cfg.unroll, &exec));
+  const int K = driver == NP_DRIVER_CHUNK ? cfg.unroll : 1;
   for (int iter = 0;; iter++) {
     if (iter > max_levels + 16) return NP_ERR_TIMEOUT;   // a level failed to advance
     if (exec) {
       NP_CK(cudaGraphLaunch(exec, s));
     } else {
-      NP_TRY(enqueue_pass(p, a, g, true, 0, s));
-      NP_TRY(enqueue_advance(w.st, 1, s));
+      for (int k = 0; k < K; k++) NP_TRY(enqueue_pass(p, a, g, true, k, s));
+      NP_TRY(enqueue_advance(w.st, K, s));
     }
     int level = 0, count = 0;
     NP_TRY(read_header(e, w, s, &level, &count));
