@@ -17,7 +17,9 @@ Other workloads (--workload): bfs-rmat20 (BFS on the same graph), bfs4k (the
 4096-vertex power-law digraph), road (a 264K-vertex grid road graph with
 out-degree <= 8: the low-nested-parallelism case, with the never-taken launch
 site measured against the same kernel without it), bt64k (Bezier tessellation
-of 65,536 curves, points/s), batched-sssp / batched-bfs (512 R-MAT instances,
+of 65,536 curves, points/s), tc-rmat17 (triangle counting on the simple
+undirected R-MAT scale-17 graph: the second CSR workload, an adjacency-
+intersection child; oriented edges/s), batched-sssp / batched-bfs (512 R-MAT instances,
 n log-uniform in [2^10, 2^20], edge factor 8..32, in one CUDA graph launch
 per step after the per-size-class autotuner; total GTEPS), serving (Poisson
 arrivals of BFS/SSSP queries from random sources over seven resident R-MAT
@@ -70,10 +72,17 @@ WORKLOADS = {
                     config=dict(workload="serving_bfs_sssp_queries_rmat_scales_16_22", graphs="R-MAT scales 16..22",
                                 edge_factor=16, weights="uint32 uniform [1,255]", mix="50/50 BFS/SSSP",
                                 arrivals="Poisson", seed=5)),
+    "tc-rmat17": dict(kind="tc", graph=None,
+                      config=dict(workload="triangle_count_rmat_scale17_undirected", vertices=1 << 17,
+                                  rmat_abcd=[0.57, 0.19, 0.19, 0.05], edge_factor=16, seed=7,
+                                  preparation="simple undirected graph, edges oriented by (degree, id)")),
     "bt64k": dict(kind="bezier", graph=None,
                   config=dict(workload="bezier_tessellation_65536_curves", curves=65536,
                               points="ceil(sqrt(kappa)*64) clamped to [4,4096]", seed=3)),
 }
+
+
+TUNED = {"bt64k": dict(child_block=32, cfactor=8)}
 
 
 def log(*a):
@@ -226,7 +235,7 @@ def ncu_traffic(kernel: str, workload: str) -> float | None:
         return None
 
 
-def kernel_bytes(kind: str, st: dict) -> dict:
+def kernel_bytes(kind: str, st: dict, W=None) -> dict:
     """Algorithmic bytes of one solve, split by kernel (per the counters `st`).
 
     SSSP parent grid: per frontier pop the id, the row_ptr pair and dist[u]
@@ -248,6 +257,13 @@ def kernel_bytes(kind: str, st: dict) -> dict:
         parent = 12 * st["parents"] + 8 * serial + 20 * st["launch_parents"] + 4 * st["pushes"]
         child = 8 * st["child_items"] + 20 * st["launch_parents"]
         solve = 20 * st["parents"] + 8 * st["items"]
+    elif kind == "tc":
+        # per parent its row bounds (8 B); per oriented edge its column, the head's row
+        # bounds and 4 B per walked out-list entry (W.walked / m of them on average)
+        per_item = 12 + 4 * W.walked / max(W.dag.m, 1)
+        parent = 8 * st["parents"] + per_item * serial + 20 * st["launch_parents"]
+        child = per_item * st["child_items"] + 20 * st["launch_parents"]
+        solve = W.bytes_per_solve()
     else:
         parent = 28 * st["parents"] + 8 * serial + 20 * st["launch_parents"]
         child = 8 * st["child_items"] + 44 * st["launch_parents"]
@@ -271,6 +287,14 @@ def run_reference(args, ws, rank):
         run = lambda: oracle.bezier(ctrl)
         units = lambda out: int(out[0][-1])
         unit = "Gpoints/s"
+    elif wl["kind"] == "tc":
+        from paper_2201_02789_gb300 import gen
+        ug, dag = gen.tc_rmat17()
+        run = lambda: oracle.triangles(ug.row_ptr, ug.col)
+        units = lambda out: dag.m
+        unit = "Gedges/s"
+        args.steps = min(args.steps, 3)
+        args.warmup = min(args.warmup, 1)
     else:
         g = load_graph(wl["graph"])
         if wl["kind"] == "sssp":
@@ -293,7 +317,7 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC if args.workload == "sssp-rmat20" else f"{unit} ({args.workload})",
             "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if wl["kind"] == "bezier" else "u32", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"bezier": "f32", "tc": "i32"}.get(wl["kind"], "u32"), "data": "synthetic",
             "config": dict(wl["config"], l2="n/a (host)"),
             "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} full solves of the workload"},
@@ -416,6 +440,65 @@ class BezierWorkload:
         return ms, 24 * 65536, 4 * 65537 + 8 * total, off_h.numpy().copy()
 
 
+class TcWorkload:
+    """Triangle counting on the degree-oriented simple undirected R-MAT-17 graph (np_triangles)."""
+
+    def __init__(self, dev, stream, ctx):
+        import torch
+        from gpu_util import DevGraph
+        from paper_2201_02789_gb300 import gen
+        from paper_2201_02789_gb300 import nestpar as npb
+        self.npb, self.stream, self.ctx, self.kind = npb, stream, ctx, "tc"
+        self.u, self.dag = gen.tc_rmat17()
+        self.dg = DevGraph(self.dag, device=dev)
+        self.out = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.unit = "Gedges/s"
+        deg = np.diff(self.dag.row_ptr.astype(np.int64))
+        src = np.repeat(np.arange(self.dag.n), deg)
+        # entries walked by the intersections: the shorter out-list of each oriented edge
+        self.walked = int(np.minimum(deg[src], deg[self.dag.col]).sum())
+
+    def solve(self, cfg, stats=False):
+        return self.npb.np_triangles(self.ctx.handle, self.dg.csr, self.out, cfg, stream=self.stream, stats=stats)
+
+    def result(self):
+        return self.out.cpu().numpy().copy()
+
+    def units(self):
+        return self.dag.m
+
+    def oracle(self):
+        import oracle
+        return np.array([oracle.triangles(self.u.row_ptr, self.u.col)], dtype=np.int64)
+
+    def bytes_per_solve(self):
+        """Row bounds per parent (8 B), per oriented edge its column and the row bounds of its
+        head (12 B), and 4 B per walked out-list entry (the searched list's reads hit L1/L2)."""
+        return 8 * self.dag.n + 12 * self.dag.m + 4 * self.walked
+
+    def e2e(self, cfg, steps, flush, dev):
+        import torch
+        rp_h = torch.from_numpy(self.dag.row_ptr).pin_memory()
+        col_h = torch.from_numpy(self.dag.col).pin_memory()
+        out_h = torch.zeros(1, dtype=torch.int64).pin_memory()
+        rp = torch.empty_like(rp_h, device=dev)
+        col = torch.empty_like(col_h, device=dev)
+        csr = self.npb.make_csr(rp, col, None, n=self.dag.n, m=self.dag.m)
+        ms = []
+        for k in range(steps + 1):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            rp.copy_(rp_h, non_blocking=True)
+            col.copy_(col_h, non_blocking=True)
+            self.npb.np_triangles(self.ctx.handle, csr, self.out, cfg, stream=self.stream)
+            out_h.copy_(self.out, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            if k:
+                ms.append((time.perf_counter() - t) * 1e3)
+        return ms, 4 * (self.dag.n + 1) + 4 * self.dag.m, 8, out_h.numpy().copy()
+
+
 def comparison_forms(npb, workload: str, cdp_steps: int):
     """(name, config, timed steps) of the forms timed beside the headline."""
     if workload == "road":
@@ -432,7 +515,7 @@ def comparison_forms(npb, workload: str, cdp_steps: int):
                 ("cdp_threshold_above_max_degree", npb.config("cdp", threshold=npb.INT32_MAX, **chunk), 5),
                 ("plain_cdp", npb.config("cdp"), cdp_steps),
                 ("t_c", npb.config("tc"), cdp_steps)]
-    graph_only = [] if workload == "bt64k" else [
+    graph_only = [] if workload in ("bt64k", "tc-rmat17") else [
         ("t_c_a_persistent", npb.config("tca", driver=npb.NP_DRIVER_PERSISTENT), 5),
         ("nodp_persistent", npb.config("nodp", driver=npb.NP_DRIVER_PERSISTENT), 5)]
     return [("plain_cdp", npb.config("cdp"), cdp_steps), ("nodp", npb.config("nodp"), cdp_steps),
@@ -460,9 +543,13 @@ def run_ours(args, ws, rank, local):
     flush = torch.empty(512 << 20, dtype=torch.int8, device=dev)
     if wl["kind"] == "bezier":
         W = BezierWorkload(dev, stream, ctx)
+    elif wl["kind"] == "tc":
+        W = TcWorkload(dev, stream, ctx)
     else:
         W = GraphWorkload(wl["kind"], load_graph(wl["graph"]), dev, stream, ctx)
-    cfg = npb.config("tca")
+    # the aggregated form; tessellation keeps the child block and coarsening factor
+    # its own sweep picked (32-thread child blocks, cfactor 8)
+    cfg = npb.config("tca", **TUNED.get(args.workload, {}))
 
     for _ in range(max(args.warmup, 3)):
         W.solve(cfg)
@@ -497,6 +584,8 @@ def run_ours(args, ws, rank, local):
     # tessellation launches init, parent and child
     if wl["kind"] == "bezier":
         per_solve = 3
+    elif wl["kind"] == "tc":
+        per_solve = 4          # level-state reset, parent, child, partial-count sum
     else:
         per_solve = 1 + st["graph_iterations"] * (2 * cfg.unroll + 1)
     gpu_launches = int(per_solve * args.steps)
@@ -536,7 +625,7 @@ def run_ours(args, ws, rank, local):
         _, pst = W.solve(cfg, stats=True)
     prof = npb.np_profile_read(ctx.handle, reset=True)
     npb.np_profile_enable(ctx.handle, False)
-    kb = kernel_bytes(wl["kind"], pst)
+    kb = kernel_bytes(wl["kind"], pst, W)
     peak, peak_kind = hbm_peak()
     kernels = {"child_agg": (prof["child_ms"], prof["child_launches"], kb["child"]),
                "parent_warp": (prof["parent_ms"], prof["parent_launches"], kb["parent"])}
@@ -582,10 +671,10 @@ def run_ours(args, ws, rank, local):
 
     line = {"metric": metric, "value": value, "unit": W.unit, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if wl["kind"] == "bezier" else "u32", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"bezier": "f32", "tc": "i32"}.get(wl["kind"], "u32"), "data": "synthetic",
             "config": dict(wl["config"], l2=L2_NOTE),
-            "form": "threshold 32 + coarsening 4 (64-thread child blocks) + grid aggregation (atomic scan), "
-                    "while-graph level loop",
+            "form": f"threshold {cfg.threshold} + coarsening {cfg.cfactor} ({cfg.child_block}-thread child blocks) "
+                    "+ grid aggregation (atomic scan), while-graph level loop",
             "ms_per_solve": {"median": statistics.median(ms), "min": min(ms)},
             "units_per_solve": units, "levels": st["levels"], "child_items": st["items"],
             "speedup_vs_plain_cdp": forms["plain_cdp"]["ms_per_solve"] / statistics.median(ms),

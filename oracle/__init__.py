@@ -1,7 +1,8 @@
 """CPU oracle (TEST INFRASTRUCTURE ONLY).
 
 Plain, slow, serial reference results for the nested-parallel workloads:
-FIFO-queue BFS, binary-heap Dijkstra and FP64 quadratic Bezier tessellation,
+FIFO-queue BFS, binary-heap Dijkstra, FP64 quadratic Bezier tessellation and
+triangle counting by its definition (every u < v < w pairwise adjacent),
 in ``oracle.c`` (compiled with gcc, ``-O2 -ffp-contract=off``) behind ctypes.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
@@ -68,6 +69,8 @@ def _load():
             lib.oracle_bezier.restype = ctypes.c_int64
             lib.oracle_bezier.argtypes = [ctypes.c_int32, _f32p, _i32p, ctypes.c_void_p,
                                           ctypes.c_int64]
+            lib.oracle_triangles.restype = ctypes.c_int64
+            lib.oracle_triangles.argtypes = [ctypes.c_int32, _i32p, _i32p]
             _lib = lib
     return _lib
 
@@ -152,3 +155,13 @@ def bezier(ctrl) -> tuple[np.ndarray, np.ndarray]:
     if rc < 0:
         raise ValueError(f"oracle_bezier failed ({rc})")
     return offsets, pts[:total]
+
+
+def triangles(row_ptr, col) -> int:
+    """Triangles of a simple undirected graph (symmetric CSR, sorted adjacency lists)."""
+    rp = _c(row_ptr, np.int32)
+    c = _c(col, np.int32) if len(col) else np.zeros(1, np.int32)
+    r = _load().oracle_triangles(int(rp.shape[0] - 1), rp, c)
+    if r < 0:
+        raise ValueError("adjacency lists must be strictly increasing")
+    return int(r)

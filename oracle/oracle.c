@@ -27,6 +27,10 @@
  *        B(t_j) = (1-t)^2 P0 + 2 (1-t) t P1 + t^2 P2 at t_j = j / (N - 1),
  *        all in FP64 (the float inputs widen exactly). Chord of length zero:
  *        N = 4096 if the second difference is non-zero, else N = 4.
+ *   TC   (the second CSR workload on the same engine; the evaluation's graph
+ *        benchmarks have an adjacency-intersection child of this shape):
+ *        the number of vertex triples {u, v, w} pairwise joined by edges of a
+ *        simple undirected graph, each triple counted once as u < v < w.
  *
  * Build with -O2 -ffp-contract=off so that no multiply-add is contracted:
  * the point count must come out of correctly rounded IEEE operations only.
@@ -237,4 +241,39 @@ int64_t oracle_bezier(int32_t ncurves, const float *ctrl, int32_t *offsets, doub
     for (int32_t j = 0; j < N; j++) oracle_bezier_point(p, N, j, points + 2 * ((size_t)offsets[c] + j));
   }
   return total;
+}
+
+/* ------------------------------------------------------------------- TC */
+
+/* Triangles of a simple undirected graph given as a symmetric CSR with sorted
+ * adjacency lists (no self-loops, no duplicate edges): every triple u < v < w
+ * with v and w adjacent to u and w adjacent to v, counted once. Returns the
+ * count, or ORACLE_EINVAL when an adjacency list is not strictly increasing. */
+static int adjacent(const int32_t *row_ptr, const int32_t *col, int32_t a, int32_t b) {
+  int64_t lo = row_ptr[a], hi = row_ptr[a + 1];
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (col[mid] < b) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < row_ptr[a + 1] && col[lo] == b;
+}
+
+int64_t oracle_triangles(int32_t n, const int32_t *row_ptr, const int32_t *col) {
+  for (int32_t u = 0; u < n; u++)
+    for (int64_t e = row_ptr[u] + 1; e < row_ptr[u + 1]; e++)
+      if (col[e] <= col[e - 1]) return ORACLE_EINVAL;
+  int64_t count = 0;
+  for (int32_t u = 0; u < n; u++) {
+    for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; e++) {
+      const int32_t v = col[e];
+      if (v <= u) continue;
+      for (int64_t f = row_ptr[v]; f < row_ptr[v + 1]; f++) {
+        const int32_t w = col[f];
+        if (w <= v) continue;
+        if (adjacent(row_ptr, col, u, w)) count++;
+      }
+    }
+  }
+  return count;
 }

@@ -129,6 +129,8 @@ struct BodyArgs {
   // graph vertex is id & vmask and per-query state is indexed by the id; a
   // single traversal has vmask = all ones.
   int vmask;
+  const int* row_ptr;            // triangle counting: row bounds of a child's vertex
+  unsigned long long* acc;       // triangle counting: kTcSlots partial counts
 };
 
 struct Args {
@@ -555,6 +557,66 @@ struct SsspBody {
       push[k] = push[k] && nd[k] < cur[k];
       if (push[k]) push[k] = atomicExch(&b.stamp[v[k]], b.L + 1) != b.L + 1;
     }
+  }
+};
+
+// Triangle counting (the second CSR workload): parent = vertex u of an
+// acyclic orientation of an undirected graph (sorted out-lists N+), child
+// item i = out-edge u -> v, which counts the w in both N+(u) and N+(v); every
+// triangle is counted once, at its edge from the lowest to the middle vertex
+// of the orientation. The shorter list is walked and each of its entries is
+// searched for in the longer one. Counts go to kTcSlots spread partial sums.
+constexpr int kTcSlots = 256;
+
+__device__ __forceinline__ bool sorted_contains(const int* a, int n, int key) {
+  int lo = 0, hi = n;   // first index with a[i] >= key
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(&a[mid]) < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < n && __ldg(&a[lo]) == key;
+}
+
+struct TcBody {
+  static constexpr bool kOffsets = false;
+  static constexpr bool kPushes = false;
+  struct P {
+    int base;
+    int n;
+  };
+  struct F {
+    int v;
+  };
+  __device__ static void count(const Args& a, int pid, int& base, int& N) {
+    base = __ldg(&a.row_ptr[pid]);
+    N = __ldg(&a.row_ptr[pid + 1]) - base;
+  }
+  __device__ static P parent(const BodyArgs&, int, int base, int N) { return P{base, N}; }
+  __device__ static F fetch(const BodyArgs& b, const P& p, int i) { return F{__ldg(&b.col[p.base + i])}; }
+  template <int K>
+  __device__ static void apply_batch(const BodyArgs& b, const P& p, const int (&)[K], const F (&f)[K],
+                                     const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
+    int vb[K], vn[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      push[k] = false;
+      v[k] = 0;
+      vb[k] = valid[k] ? __ldg(&b.row_ptr[f[k].v]) : 0;
+      vn[k] = valid[k] ? __ldg(&b.row_ptr[f[k].v + 1]) - vb[k] : 0;
+    }
+    unsigned c = 0;
+    const int* nu = b.col + p.base;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      const int* nv = b.col + vb[k];
+      const bool walk_u = p.n <= vn[k];
+      const int* walk = walk_u ? nu : nv;
+      const int* look = walk_u ? nv : nu;
+      const int nw = walk_u ? p.n : vn[k], nl = walk_u ? vn[k] : p.n;
+      for (int t = 0; t < nw; t++) c += sorted_contains(look, nl, __ldg(&walk[t])) ? 1u : 0u;
+    }
+    if (c) atomicAdd(&b.acc[blockIdx.x & (kTcSlots - 1)], (unsigned long long)c);
   }
 };
 

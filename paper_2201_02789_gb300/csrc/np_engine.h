@@ -153,6 +153,8 @@ __global__ void fill_unreached_kernel(int kind, long long total, int* level, uns
 __global__ void seed_sources_kernel(LevelState* st, int kind, const int* ids, int nsrc, int* level, unsigned* dist,
                                     int* fr0, int max_levels);
 __global__ void advance_base_kernel(LevelState* st, int K);
+// *out (+)= the sum of part[0, n) (one block)
+__global__ void sum_u64_kernel(const unsigned long long* part, int n, unsigned long long* out, int accumulate);
 // Sets *bad when a CSR breaks its contract: row_ptr[0] != 0, row_ptr[n] != m,
 // a decreasing row_ptr, or a column index outside [0, n).
 __global__ void csr_check_kernel(const int* row_ptr, const int* col, int n, long long m, int* bad);

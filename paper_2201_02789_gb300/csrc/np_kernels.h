@@ -29,5 +29,6 @@ struct BodyKernels {
 const BodyKernels& bfs_kernels();
 const BodyKernels& sssp_kernels();
 const BodyKernels& bezier_kernels();
+const BodyKernels& tc_kernels();
 
 }  // namespace nestpar

@@ -337,6 +337,33 @@ def random_sources(g: Csr, count: int, seed: int) -> np.ndarray:
     return cand[idx].astype(np.int32)
 
 
+def undirected_simple(g: Csr) -> Csr:
+    """The simple undirected graph under a digraph: both directions of every
+    edge, self-loops and duplicates dropped, adjacency lists sorted (no weights)."""
+    src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr.astype(np.int64)))
+    dst = g.col.astype(np.int64)
+    keep = src != dst
+    a = np.concatenate([src[keep], dst[keep]])
+    b = np.concatenate([dst[keep], src[keep]])
+    key = np.unique(a * g.n + b)
+    row_ptr, col = _csr_from_edges(g.n, key // g.n, key % g.n)
+    return Csr(g.n, row_ptr, col)
+
+
+def oriented_by_degree(u: Csr) -> Csr:
+    """An acyclic orientation of a simple undirected graph: each edge points from
+    the endpoint of lower (degree, id) to the other; out-lists sorted by id. Input
+    preparation for triangle counting (keeps high-degree vertices' out-lists short)."""
+    deg = np.diff(u.row_ptr.astype(np.int64))
+    src = np.repeat(np.arange(u.n, dtype=np.int64), deg)
+    dst = u.col.astype(np.int64)
+    rank = np.empty(u.n, dtype=np.int64)
+    rank[np.lexsort((np.arange(u.n), deg))] = np.arange(u.n)
+    fwd = rank[src] < rank[dst]
+    row_ptr, col = _csr_from_edges(u.n, src[fwd], dst[fwd])
+    return Csr(u.n, row_ptr, col)
+
+
 # ---- named workloads ------------------------------------------------------------------
 
 def bfs4k() -> Csr:
@@ -347,6 +374,13 @@ def bfs4k() -> Csr:
 def rmat20() -> Csr:
     """SSSP/BFS workload: R-MAT scale 20, edge factor 16, (.57,.19,.19,.05), weights 1..255, seed 2."""
     return rmat(20, 16, 0.57, 0.19, 0.19, seed=2)
+
+
+def tc_rmat17() -> tuple[Csr, Csr]:
+    """Triangle-counting workload: the simple undirected graph under R-MAT scale 17, edge
+    factor 16 (Graph500 probabilities, seed 7), and its degree orientation."""
+    u = undirected_simple(rmat(17, 16, seed=7, weights=None))
+    return u, oriented_by_degree(u)
 
 
 def bt64k() -> np.ndarray:

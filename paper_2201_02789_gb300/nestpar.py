@@ -25,7 +25,8 @@ NP_GRAN_NONE, NP_GRAN_WARP, NP_GRAN_BLOCK, NP_GRAN_MULTIBLOCK, NP_GRAN_GRID_DEVI
 NP_SCAN_LOOKBACK, NP_SCAN_ATOMIC = 0, 1
 NP_DRIVER_AUTO, NP_DRIVER_HOST, NP_DRIVER_CHUNK, NP_DRIVER_WHILE, NP_DRIVER_PERSISTENT = range(5)
 NP_COUNT_CSR_DEGREE, NP_COUNT_BEZIER = 0, 1
-NP_BODY_BFS_VISIT, NP_BODY_SSSP_RELAX, NP_BODY_BEZIER_EVAL = 0, 1, 2
+NP_BODY_BFS_VISIT, NP_BODY_SSSP_RELAX, NP_BODY_BEZIER_EVAL, NP_BODY_TRIANGLES = 0, 1, 2, 3
+NP_TRI_SLOTS = 256
 NP_BATCH_BFS, NP_BATCH_SSSP = 0, 1
 INT32_MAX = 2 ** 31 - 1
 
@@ -107,7 +108,7 @@ class np_body(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("level", ctypes.c_void_p), ("dist", ctypes.c_void_p),
                 ("stamp", ctypes.c_void_p), ("next", ctypes.c_void_p), ("next_count", ctypes.c_void_p),
                 ("ctrl", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("points", ctypes.c_void_p),
-                ("cap", ctypes.c_int64)]
+                ("cap", ctypes.c_int64), ("tri_counts", ctypes.c_void_p)]
 
 
 class np_batch_options(ctypes.Structure):
@@ -181,6 +182,7 @@ _SIGS = {
     "np_server_step": [_VP, ctypes.POINTER(ctypes.c_int32)],
     "np_server_poll": [_VP, _I64, ctypes.POINTER(np_query_info)],
     "np_server_finished": [_VP, _VP, _I32, ctypes.POINTER(ctypes.c_int32)],
+    "np_triangles": [_VP, ctypes.POINTER(np_csr), _VP, ctypes.POINTER(np_config), _VP, ctypes.POINTER(np_stats)],
     "np_status_string": [_I32],
     "np_version": [],
 }
@@ -386,6 +388,14 @@ def np_bezier_host(ctx, ctrl, ncurves: int, offsets_out, points_out, cap: int, c
 
 
 # ------------------------------------------------------------ configurations
+
+def np_triangles(ctx, dag: np_csr, count, cfg=None, stream=None, stats: bool = False, check: bool = True):
+    st, want = _stats_arg(stats)
+    s = lib().np_triangles(ctx, ctypes.byref(dag), _ptr(count), ctypes.byref(_cfg(cfg)), _stream(stream),
+                           ctypes.byref(st) if want else None)
+    _check(s, "np_triangles", check)
+    return (s, st.as_dict()) if want else s
+
 
 def np_bfs_multi(ctx, g: np_csr, sources, level, ld: int, cfg=None, stream=None, stats: bool = False,
                  check: bool = True):
