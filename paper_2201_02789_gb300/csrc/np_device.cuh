@@ -43,8 +43,12 @@
 #endif
 #ifdef NP_CHILD_MAXREG
 #define NP_CHILD_BOUNDS __maxnreg__(NP_CHILD_MAXREG)
+#define NP_CHILD_AGG_BOUNDS(CF) __maxnreg__(NP_CHILD_MAXREG)
 #else
 #define NP_CHILD_BOUNDS __launch_bounds__(1024)
+// the aggregated child grid with up to 4 blocks per coarsened block fits in 48
+// registers without spilling: five 256-thread CTAs per SM instead of four
+#define NP_CHILD_AGG_BOUNDS(CF) __maxnreg__((CF) <= 4 ? 48 : 64)
 #endif
 #ifdef NP_PARENT_MAXREG
 #define NP_PARENT_BOUNDS __maxnreg__(NP_PARENT_MAXREG)
@@ -632,7 +636,7 @@ struct BezierBody {
   struct F {};
   // Point count in FP64 with correctly rounded operations only, so that it is
   // bit-identical to a serial FP64 evaluation (no contraction into FMA).
-  __device__ static int point_count(const float* p) {
+  __device__ static int point_count_fp64(const float* p) {
     const double x0 = p[0], y0 = p[1], x1 = p[2], y1 = p[3], x2 = p[4], y2 = p[5];
     const double sx = __dadd_rn(__dsub_rn(x0, __dmul_rn(2.0, x1)), x2);
     const double sy = __dadd_rn(__dsub_rn(y0, __dmul_rn(2.0, y1)), y2);
@@ -645,6 +649,46 @@ struct BezierBody {
     if (t < 4.0) return 4;
     if (t > 4096.0) return 4096;
     return (int)t;
+  }
+  // The same count without FP64 arithmetic where that is provably the same
+  // number (FP64 throughput is low on this GPU). When every coordinate is
+  // k * 2^-24 with 0 <= k < 2^24, the FP64 second difference, chord and their
+  // squared norms above are exact: s2 = S * 2^-48 and c2 = C * 2^-48 with
+  // integers S < 2^53, C < 2^49. The exact t = 64 (S / C)^(1/4) then has
+  // ceil(t) = the least m with m^4 C >= 2^24 S, found with 128-bit integers;
+  // the FP64 evaluation carries a relative error below 3e-16 (four correctly
+  // rounded operations), so it has the same ceiling unless t^4 lies within a
+  // relative 2^-40 of m^4 or (m-1)^4, where the FP64 sequence itself decides.
+  // Other inputs also take the FP64 sequence.
+  __device__ static int point_count(const float* p) {
+    unsigned k[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+      const float f = p[i] * 16777216.0f;   // exact: a power-of-two scale
+      if (!(f >= 0.0f && f < 16777216.0f && f == truncf(f))) return point_count_fp64(p);
+      k[i] = (unsigned)f;
+    }
+    const long long sx = (long long)k[0] - 2ll * k[2] + k[4], sy = (long long)k[1] - 2ll * k[3] + k[5];
+    const long long cx = (long long)k[4] - k[0], cy = (long long)k[5] - k[1];
+    const unsigned long long S = (unsigned long long)(sx * sx) + (unsigned long long)(sy * sy);
+    const unsigned long long C = (unsigned long long)(cx * cx) + (unsigned long long)(cy * cy);
+    if (C == 0) return S > 0 ? 4096 : 4;
+    if (S == 0) return 4;                                   // t = 0 exactly, in FP64 too
+    using u128 = unsigned __int128;
+    const u128 A = (u128)S << 24;                          // t^4 * C
+    auto q4 = [&](unsigned long long m) -> u128 { const u128 m2 = (u128)(m * m); return m2 * m2 * C; };
+    if (A > q4(4097)) return 4096;                          // t > 4097: clamped, far from any tie
+    // estimate, then the exact ceiling by at most a few integer steps
+    unsigned long long m = (unsigned long long)ceilf(64.0f * sqrtf(sqrtf((float)S / (float)C)));
+    if (m < 1) m = 1;
+    if (m > 4097) m = 4097;
+    for (int it = 0; it < 8 && m > 1 && A <= q4(m - 1); it++) m--;
+    for (int it = 0; it < 8 && A > q4(m); it++) m++;
+    const u128 hi = q4(m), lo = q4(m - 1);
+    const bool exact_m = A <= hi && A > lo;
+    const bool near = (hi - A) <= (hi >> 40) || (m > 1 && (A - lo) <= (lo >> 40));
+    if (!exact_m || near) return point_count_fp64(p);
+    return m < 4 ? 4 : (m > 4096 ? 4096 : (int)m);
   }
   __device__ static void count(const Args& a, int pid, int& base, int& N) {
     base = 0;
@@ -754,17 +798,32 @@ __device__ __forceinline__ void child_agg_run(const BodyArgs& b, const int4* rec
   const int first = sub * chunk;
   const int last = min(total, first + chunk);
   int j = -1, next_off = 0, off = 0, N = 0;
+  // record j + 1 and the offset of record j + 2, loaded one record ahead
+  int4 rn = make_int4(0, 0, 0, 0);
+  int next2 = 0x7fffffff;
   typename Body::P p{};
   __syncthreads();
   StageSink sink{b.next, b.next_count, s_stage, s_stage_n};
   for (int B0 = first; B0 < last; B0++) {
     if (j < 0 || B0 >= next_off) {
-      j = j < 0 ? warp_search(boff, 0, nrec, B0) : warp_search_near(boff, j + 1, nrec, B0);
-      const int4 r = __ldcg(&rec[j]);
-      off = __ldcg(&boff[j]);
-      next_off = j + 1 < nrec ? __ldcg(&boff[j + 1]) : 0x7fffffff;
+      int4 r;
+      if (j >= 0 && B0 < next2) {
+        // blocks are contiguous and a launching parent has at least one block,
+        // so the next record is j + 1, already loaded
+        j++;
+        r = rn;
+        off = next_off;
+        next_off = next2;
+      } else {
+        j = j < 0 ? warp_search(boff, 0, nrec, B0) : warp_search_near(boff, j + 1, nrec, B0);
+        r = __ldcg(&rec[j]);
+        off = __ldcg(&boff[j]);
+        next_off = j + 1 < nrec ? __ldcg(&boff[j + 1]) : 0x7fffffff;
+      }
       N = r.z;
       p = Body::parent(b, r.x, r.y, r.z);
+      if (j + 1 < nrec) rn = __ldcg(&rec[j + 1]);
+      next2 = j + 2 < nrec ? __ldcg(&boff[j + 2]) : 0x7fffffff;
     }
     run_coarsened<Body, CF>(b, p, N, B0 - off, cb, stid, sink);
   }
@@ -791,7 +850,7 @@ __device__ __forceinline__ void agg_totals(const LevelState* st, int L, int mode
 // the stream-ordered persistent grid of the grid-host form, whose level and
 // totals are read from the level state.
 template <class Body, int CF>
-__global__ void NP_CHILD_BOUNDS child_agg(BodyArgs b, AggSeg s) {
+__global__ void NP_CHILD_AGG_BOUNDS(CF) child_agg(BodyArgs b, AggSeg s) {
   __shared__ int s_stage[kCtaStage];
   __shared__ int s_stage_n, s_stage_base;
   int nrec = s.nrec, total = s.total;

@@ -224,6 +224,37 @@ def test_bezier_hand_counts_on_gpu(ctx):
     np.testing.assert_array_equal(np.diff(off), [int(r[6]) for r in rows])
 
 
+def _tie_curves():
+    """Curves on the 2^-24 grid whose exact t = 64 (S/C)^(1/4) is an integer m (P0 = (0, m^2),
+    P1 = (4096, 0), P2 = (8192, m^2) in units of 2^-24), and the same with the apex moved by
+    one unit either way (t within about 1/m^2 of m)."""
+    rows = []
+    for m in (3, 4, 5, 17, 64, 100, 1000, 4095, 4096):
+        for d in (0, -1, 1):
+            y = m * m + d
+            if not 0 <= y < (1 << 24):
+                continue
+            rows.append([0, y, 4096, 0, 8192, y])
+    return np.array(rows, np.float64).astype(np.float32).reshape(-1, 3, 2) * np.float32(2.0 ** -24)
+
+
+@pytest.mark.parametrize("form", ["tca", "nodp"])
+def test_bezier_counts_at_ties_and_off_grid(ctx, form):
+    """The point count takes an exact integer path for coordinates on the 2^-24 grid and the
+    FP64 sequence elsewhere and at near-ties; both must give the oracle's FP64 counts."""
+    ties = _tie_curves()
+    u = gen.uniform_f64(77, 1, 0, 600 * 6)
+    off_grid = np.concatenate([
+        ((u[:1800] - 0.5) * 6.0).astype(np.float32),          # negative and > 1 coordinates
+        (u[1800:] * 0.3 + 0.1).astype(np.float32)]).reshape(-1, 3, 2)   # values off the 2^-24 grid
+    straight = np.array([[[0.25, 0.25], [0.5, 0.5], [0.75, 0.75]], [[0.5, 0.5]] * 3,
+                         [[0.0, 0.0], [0.0, 0.5], [0.0, 0.0]]], np.float32)
+    for ctrl in (ties, off_grid, straight, np.concatenate([ties, gen.bezier_curves(300, seed=78)])):
+        status, off, pts, _ = bezier(ctx, ctrl, npb.config(form))
+        assert status == npb.NP_OK
+        np.testing.assert_array_equal(off, oracle.bezier_offsets(ctrl))
+
+
 def test_bezier_capacity_and_empty(ctx):
     ctrl = gen.bezier_curves(200, seed=32)
     ref_off, ref_pts = oracle.bezier(ctrl)
