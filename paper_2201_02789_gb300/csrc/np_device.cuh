@@ -85,6 +85,7 @@ struct __align__(16) LevelState {
   unsigned long long s[S_N];     // counters (np_stats)
   int body_iters;                // conditional-while iterations of this solve (bounded)
   int pad;
+  int child_ticket[4];           // slot L % 4: next chunk of aggregated blocks (balanced bodies)
   unsigned bar_count;            // grid barrier of the persistent level loop: arrivals
   unsigned bar_gen;              // and generation
 };
@@ -109,6 +110,7 @@ __device__ __forceinline__ void level_open(LevelState* st, int L, int count) {
   st->agg_records[s2] = 0;
   st->agg_blocks[s2] = 0;
   st->agg_acc[s2] = 0ull;
+  st->child_ticket[s2] = 0;
   st->count[(L + 2) % 3] = 0;
   if (count > 0) {
     atomicAdd(&st->s[S_LEVELS], 1ull);
@@ -482,6 +484,7 @@ struct CtaSink {
 struct BfsBody {
   static constexpr bool kOffsets = false;
   static constexpr bool kPushes = true;
+  static constexpr bool kBalance = false;   // child blocks cost the same: static ranges
   struct P {
     int base;
     int qbase;   // query part of the ids of this parent's children
@@ -519,6 +522,7 @@ struct BfsBody {
 struct SsspBody {
   static constexpr bool kOffsets = false;
   static constexpr bool kPushes = true;
+  static constexpr bool kBalance = false;
   struct P {
     int base;
     unsigned du;
@@ -585,6 +589,7 @@ __device__ __forceinline__ bool sorted_contains(const int* a, int n, int key) {
 struct TcBody {
   static constexpr bool kOffsets = false;
   static constexpr bool kPushes = false;
+  static constexpr bool kBalance = true;    // block cost varies with the lists' lengths
   struct P {
     int base;
     int n;
@@ -628,6 +633,7 @@ struct TcBody {
 struct BezierBody {
   static constexpr bool kOffsets = true;
   static constexpr bool kPushes = false;
+  static constexpr bool kBalance = false;
   struct P {
     float x0, y0, x1, y1, x2, y2;
     int base;
@@ -780,6 +786,42 @@ __global__ void NP_CHILD_BOUNDS child_direct(BodyArgs b, int pid, int base, int 
   run_coarsened<Body, CF>(b, p, N, blockIdx.x, blockDim.x, threadIdx.x, sink);
 }
 
+// Persistent aggregated child grid for bodies whose blocks differ widely in
+// cost: each CTA takes the next blockDim.x / cb aggregated blocks from the
+// level's ticket (one child block per sub-block) until none are left. A
+// sub-block's blocks only move forward, so the parent search continues from
+// the last record. Bodies without appends only (no staging).
+template <class Body, int CF>
+__device__ __forceinline__ void child_agg_balanced(const BodyArgs& b, const int4* rec, const int* boff, int nrec,
+                                                   int total, int cb, int* ticket, int* s_next) {
+  const int per_cta = (int)blockDim.x / cb;
+  const int local = (int)threadIdx.x / cb, stid = (int)threadIdx.x % cb;
+  int j = -1, next_off = 0, off = 0, N = 0, done = 0;
+  typename Body::P p{};
+  WarpSink sink{b.next, b.next_count};
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) *s_next = atomicAdd(ticket, per_cta);
+    __syncthreads();
+    const int first = *s_next;
+    if (first >= total) break;
+    const int B0 = first + local;
+    if (B0 < total) {
+      if (j < 0 || B0 >= next_off) {
+        j = j < 0 ? warp_search(boff, 0, nrec, B0) : warp_search_near(boff, j + 1, nrec, B0);
+        const int4 r = __ldcg(&rec[j]);
+        off = __ldcg(&boff[j]);
+        next_off = j + 1 < nrec ? __ldcg(&boff[j + 1]) : 0x7fffffff;
+        N = r.z;
+        p = Body::parent(b, r.x, r.y, r.z);
+      }
+      run_coarsened<Body, CF>(b, p, N, B0 - off, cb, stid, sink);
+      done++;
+    }
+  }
+  if (stid == 0 && done) add_stat(b.st, S_CBLOCKS, (unsigned long long)done);
+}
+
 // Aggregated child blocks [0, total) of the records rec[0, nrec) with block
 // offsets boff: disaggregation + coarsened body. A CTA hosts blockDim.x / cb
 // child blocks of cb threads that run independently (no CTA barrier on this
@@ -790,7 +832,13 @@ __global__ void NP_CHILD_BOUNDS child_direct(BodyArgs b, int pid, int base, int 
 template <class Body, int CF>
 __device__ __forceinline__ void child_agg_run(const BodyArgs& b, const int4* rec, const int* boff, int nrec,
                                               int total, int cb, bool count_blocks, int* s_stage, int* s_stage_n,
-                                              int* s_stage_base) {
+                                              int* s_stage_base, int* ticket = nullptr) {
+  if constexpr (Body::kBalance) {
+    if (ticket) {
+      child_agg_balanced<Body, CF>(b, rec, boff, nrec, total, cb, ticket, s_stage_n);
+      return;
+    }
+  }
   if (threadIdx.x == 0) *s_stage_n = 0;
   const int per_cta = (int)blockDim.x / cb;
   const int sub = (int)blockIdx.x * per_cta + (int)threadIdx.x / cb, stid = (int)threadIdx.x % cb;
@@ -864,7 +912,8 @@ __global__ void NP_CHILD_AGG_BOUNDS(CF) child_agg(BodyArgs b, AggSeg s) {
     }
     agg_totals(b.st, L, s.mode, nrec, total);
   }
-  child_agg_run<Body, CF>(b, s.rec, s.boff, nrec, total, s.cb, s.mode != 0, s_stage, &s_stage_n, &s_stage_base);
+  child_agg_run<Body, CF>(b, s.rec, s.boff, nrec, total, s.cb, s.mode != 0, s_stage, &s_stage_n, &s_stage_base,
+                          s.mode != 0 ? &b.st->child_ticket[b.L & 3] : nullptr);
 }
 
 // --------------------------------------------------------------- parent side
@@ -1321,7 +1370,7 @@ __global__ void __launch_bounds__(1024) level_loop(Args a, int max_levels) {
       int nrec = 0, total = 0;
       agg_totals(st, L, a.scan == 0 ? 1 : 2, nrec, total);
       child_agg_run<Body, CF>(b, a.rec, a.boff, nrec, total, a.child_block, true, s_stage, &s_stage_n,
-                              &s_stage_base);
+                              &s_stage_base, &st->child_ticket[L & 3]);
     }
     if (!grid_barrier(st, &s_ok)) break;
     L++;

@@ -42,6 +42,7 @@ __device__ __forceinline__ void reset_slots(LevelState* st) {
     st->agg_records[k] = 0;
     st->agg_blocks[k] = 0;
     st->agg_acc[k] = 0ull;
+    st->child_ticket[k] = 0;
   }
   for (int k = 0; k < S_N; k++) st->s[k] = 0ull;
   st->body_iters = 0;

@@ -59,6 +59,7 @@ __global__ void noalloc_reset_kernel(LevelState* st) {
     st->agg_records[k] = 0;
     st->agg_blocks[k] = 0;
     st->agg_acc[k] = 0ull;
+    st->child_ticket[k] = 0;
   }
   st->error = 0u;
   for (int k = 0; k < S_N; k++) st->s[k] = 0ull;
