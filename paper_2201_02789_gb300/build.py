@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libnestpar.so")
 SOURCES = ["np_capi.cu", "np_engine.cu", "np_batch.cu", "np_server.cu", "np_bfs.cu", "np_sssp.cu", "np_bezier.cu",
-           "np_tc.cu", "np_noalloc.cu"]
+           "np_tc.cu", "np_sssp64.cu", "np_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-rdc=true", "-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

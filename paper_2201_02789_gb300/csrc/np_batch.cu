@@ -46,6 +46,7 @@ struct Group {
   int* col = nullptr;
   unsigned* w = nullptr;
   int* ids = nullptr;           // union ids of the instances' sources
+  unsigned long long* dtag = nullptr;   // SSSP: packed distance and append tag per vertex
   int nsrc = 0;
   unsigned char* mem = nullptr;
   Workspace ws;
@@ -99,7 +100,8 @@ void drop_batch_graph(np_batch* b) {
   b->graph_out = nullptr;
 }
 
-const BodyKernels& kernels_of(int kind) { return kind == 0 ? bfs_kernels() : sssp_kernels(); }
+// SSSP groups run in the packed form (distance and append tag in one word)
+const BodyKernels& kernels_of(int kind) { return kind == 0 ? bfs_kernels() : sssp64_kernels(); }
 
 void group_args(np_batch* b, Group& g, const np_config& cfg, void* out, Args& a) {
   base_args(g.ws, cfg, a);
@@ -109,14 +111,29 @@ void group_args(np_batch* b, Group& g, const np_config& cfg, void* out, Args& a)
   a.b.level = b->kind == 0 ? reinterpret_cast<int*>(out) + g.vbase : nullptr;
   a.b.dist = b->kind == 1 ? reinterpret_cast<unsigned*>(out) + g.vbase : nullptr;
   a.b.stamp = wsp<int>(g.ws, g.ws.lay.off_stamp);
+  a.b.dtag = g.dtag;
 }
 
 // fill + seed for one group on stream s (used by the tuner)
 np_status enqueue_group_init(np_batch* b, Group& g, const Args& a, cudaStream_t s) {
-  fill_unreached_kernel<<<blocks_for(g.n), 256, 0, s>>>(b->kind, g.n, a.b.level, a.b.dist, a.b.stamp);
+  if (b->kind == 1) {
+    init_dtag_kernel<<<blocks_for(g.n), 256, 0, s>>>(g.n, g.dtag);
+    NP_CK(cudaGetLastError());
+    seed_dtag_kernel<<<blocks_for(g.nsrc), 256, 0, s>>>(g.ws.st, g.ids, g.nsrc, g.dtag, a.fr0, g.n + 2);
+  } else {
+    fill_unreached_kernel<<<blocks_for(g.n), 256, 0, s>>>(b->kind, g.n, a.b.level, a.b.dist, a.b.stamp);
+    NP_CK(cudaGetLastError());
+    seed_sources_kernel<<<blocks_for(g.nsrc), 256, 0, s>>>(g.ws.st, b->kind, g.ids, g.nsrc, a.b.level, a.b.dist,
+                                                           a.fr0, g.n + 2);
+  }
   NP_CK(cudaGetLastError());
-  seed_sources_kernel<<<blocks_for(g.nsrc), 256, 0, s>>>(g.ws.st, b->kind, g.ids, g.nsrc, a.b.level, a.b.dist,
-                                                         a.fr0, g.n + 2);
+  return NP_OK;
+}
+
+// SSSP: the group's distances out of the packed state
+np_status enqueue_group_result(np_batch* b, Group& g, const Args& a, cudaStream_t s) {
+  if (b->kind != 1) return NP_OK;
+  dtag_to_dist_kernel<<<blocks_for(g.n), 256, 0, s>>>(g.n, g.dtag, a.b.dist);
   NP_CK(cudaGetLastError());
   return NP_OK;
 }
@@ -150,18 +167,29 @@ np_status build_batch_graph(np_batch* b, void* out) {
     unsigned* dist = a.b.dist;
     int* stamp = a.b.stamp;
     void* fill_args[] = {&kind, &total, &level, &dist, &stamp};
-    cudaGraphNode_t n1, n2, n3;
-    np_status st = add_kernel_node(graph, nullptr, 0, (const void*)fill_unreached_kernel, blocks_for(g.n), 256,
-                                   fill_args, &n1);
+    unsigned long long* dtag = g.dtag;
+    void* fill64_args[] = {&total, &dtag};
+    cudaGraphNode_t n1, n2, n3, n4;
+    np_status st = kind == 1 ? add_kernel_node(graph, nullptr, 0, (const void*)init_dtag_kernel, blocks_for(g.n), 256,
+                                               fill64_args, &n1)
+                             : add_kernel_node(graph, nullptr, 0, (const void*)fill_unreached_kernel, blocks_for(g.n),
+                                               256, fill_args, &n1);
     LevelState* lst = g.ws.st;
     const int* ids = g.ids;
     int nsrc = g.nsrc;
     int* fr0 = a.fr0;
     int maxl = g.n + 2;
     void* seed_args[] = {&lst, &kind, &ids, &nsrc, &level, &dist, &fr0, &maxl};
+    void* seed64_args[] = {&lst, &ids, &nsrc, &dtag, &fr0, &maxl};
     if (st == NP_OK)
-      st = add_kernel_node(graph, &n1, 1, (const void*)seed_sources_kernel, blocks_for(g.nsrc), 256, seed_args, &n2);
+      st = kind == 1 ? add_kernel_node(graph, &n1, 1, (const void*)seed_dtag_kernel, blocks_for(g.nsrc), 256,
+                                       seed64_args, &n2)
+                     : add_kernel_node(graph, &n1, 1, (const void*)seed_sources_kernel, blocks_for(g.nsrc), 256,
+                                       seed_args, &n2);
     if (st == NP_OK) st = add_while_node(b->e, g.ws.st, graph, &n2, 1, p, a, gr, cfg.unroll, &n3);
+    void* out64_args[] = {&total, &dtag, &dist};
+    if (st == NP_OK && kind == 1)
+      st = add_kernel_node(graph, &n3, 1, (const void*)dtag_to_dist_kernel, blocks_for(g.n), 256, out64_args, &n4);
     if (st != NP_OK) {
       cudaGraphDestroy(graph);
       return st;
@@ -223,6 +251,7 @@ np_status time_class(np_batch* b, int ci, const np_config& cfg, void* out, int r
       group_args(b, g, cfg, out, a);
       NP_TRY(enqueue_group_init(b, g, a, s));
       NP_TRY(run_levels(b->e, g.ws, p, a, cfg, g.n, g.n + 2, s));
+      NP_TRY(enqueue_group_result(b, g, a, s));
     }
     NP_CK(cudaEventRecord(b->e.ev[1], s));
     NP_CK(cudaEventSynchronize(b->e.ev[1]));
@@ -330,7 +359,8 @@ np_status np_batch_create(np_ctx* ctx, int32_t count, const np_csr* graphs, cons
     const size_t brp = align_up(sizeof(int) * ((size_t)g.n + 1)), bcol = align_up(sizeof(int) * (size_t)g.m);
     const size_t bw = opt->kind == NP_BATCH_SSSP ? align_up(sizeof(unsigned) * (size_t)g.m) : 0;
     const size_t bids = align_up(sizeof(int) * (size_t)g.nsrc);
-    st = from_cuda(cudaMalloc(&g.mem, brp + bcol + bw + bids + kAlign));
+    const size_t bd64 = opt->kind == NP_BATCH_SSSP ? align_up(sizeof(unsigned long long) * (size_t)g.n) : 0;
+    st = from_cuda(cudaMalloc(&g.mem, brp + bcol + bw + bids + bd64 + kAlign));
     if (st == NP_OK) st = ws_init(g.ws);
     if (st == NP_OK) st = ws_ensure(g.ws, g.n);
     if (st != NP_OK) {
@@ -341,6 +371,7 @@ np_status np_batch_create(np_ctx* ctx, int32_t count, const np_csr* graphs, cons
     g.col = reinterpret_cast<int*>(g.mem + brp);
     g.w = bw ? reinterpret_cast<unsigned*>(g.mem + brp + bcol) : nullptr;
     g.ids = reinterpret_cast<int*>(g.mem + brp + bcol + bw);
+    g.dtag = bd64 ? reinterpret_cast<unsigned long long*>(g.mem + brp + bcol + bw + bids) : nullptr;
     std::vector<int> ids;
     int voff = 0;
     long long eoff = 0;

@@ -20,6 +20,8 @@ struct np_ctx {
   int* ids = nullptr;                 // device copy of the sources of a multi-source solve
   int ids_cap = 0;
   unsigned long long* tri = nullptr;  // triangle-counting partial sums [kTcSlots]
+  unsigned long long* dtag = nullptr; // packed SSSP state (dist << 32 | tag) of np_sssp / np_sssp_multi
+  int64_t dtag_cap = 0;
   // device staging for the *_host entry points
   unsigned char* stage = nullptr;
   size_t stage_bytes = 0;
@@ -29,6 +31,19 @@ struct np_ctx {
 int nestpar_ctx_device(const np_ctx* c) { return c->e.device; }
 
 namespace {
+
+np_status ensure_dtag(np_ctx* c, int64_t total) {
+  if (total <= c->dtag_cap) return NP_OK;
+  if (c->dtag) {
+    NP_CK(cudaDeviceSynchronize());
+    cudaFree(c->dtag);
+    c->dtag = nullptr;
+    c->dtag_cap = 0;
+  }
+  NP_CK(cudaMalloc(&c->dtag, sizeof(unsigned long long) * (size_t)total));
+  c->dtag_cap = total;
+  return NP_OK;
+}
 
 constexpr int kVersion = 10100;  // 1.1.0
 
@@ -46,7 +61,8 @@ np_status solve(np_ctx* c, int kind, const np_csr* g, int src, int* level, unsig
   NP_CK(cudaSetDevice(c->e.device));
   st = ws_ensure(c->w, g->n);
   if (st != NP_OK) return st;
-  const BodyKernels& K = kind == 0 ? bfs_kernels() : sssp_kernels();
+  // SSSP runs in the packed form (distance and append tag in one word)
+  const BodyKernels& K = kind == 0 ? bfs_kernels() : sssp64_kernels();
   Plan p = make_plan(K, *cfg);
   Args a;
   base_args(c->w, *cfg, a);
@@ -56,9 +72,16 @@ np_status solve(np_ctx* c, int kind, const np_csr* g, int src, int* level, unsig
   a.b.level = level;
   a.b.dist = dist;
   a.b.stamp = wsp<int>(c->w, c->w.lay.off_stamp);
+  if (kind == 1) {
+    NP_TRY(ensure_dtag(c, g->n));
+    a.b.dtag = c->dtag;
+  }
   const int blocks = (int)((g->n + 255) / 256 < 4096 ? (g->n + 255) / 256 : 4096);
   if (c->e.profile) NP_CK(cudaEventRecord(c->e.ev[0], s));
-  init_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, kind, g->n, src, level, dist, a.b.stamp, a.fr0, g->n + 2);
+  if (kind == 1)
+    init_dtag_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, g->n, src, c->dtag, a.fr0, g->n + 2);
+  else
+    init_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, kind, g->n, src, level, dist, a.b.stamp, a.fr0, g->n + 2);
   NP_CK(cudaGetLastError());
   if (c->e.profile) {
     NP_CK(cudaEventRecord(c->e.ev[3], s));
@@ -71,6 +94,10 @@ np_status solve(np_ctx* c, int kind, const np_csr* g, int src, int* level, unsig
   c->e.prof_next_parents = 1;
   st = run_levels(c->e, c->w, p, a, *cfg, g->n, g->n + 2, s);
   if (st != NP_OK) return st;
+  if (kind == 1) {
+    dtag_to_dist_kernel<<<blocks, 256, 0, s>>>(g->n, c->dtag, dist);
+    NP_CK(cudaGetLastError());
+  }
   return finish(c->e, c->w, s, stats);
 }
 
@@ -104,7 +131,7 @@ np_status solve_multi(np_ctx* c, int kind, const np_csr* g, int nsrc, const int3
     c->ids_cap = nsrc;
   }
   NP_CK(cudaMemcpyAsync(c->ids, ids.data(), sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, s));
-  const BodyKernels& K = kind == 0 ? bfs_kernels() : sssp_kernels();
+  const BodyKernels& K = kind == 0 ? bfs_kernels() : sssp64_kernels();
   Plan p = make_plan(K, *cfg);
   Args a;
   base_args(c->w, *cfg, a);
@@ -115,12 +142,24 @@ np_status solve_multi(np_ctx* c, int kind, const np_csr* g, int nsrc, const int3
   a.b.dist = dist;
   a.b.stamp = wsp<int>(c->w, c->w.lay.off_stamp);
   a.b.vmask = (int)(ld - 1);
-  fill_unreached_kernel<<<blocks_for(total), 256, 0, s>>>(kind, total, level, dist, a.b.stamp);
-  NP_CK(cudaGetLastError());
-  seed_sources_kernel<<<blocks_for(nsrc), 256, 0, s>>>(c->w.st, kind, c->ids, nsrc, level, dist, a.fr0, g->n + 2);
+  if (kind == 1) {
+    NP_TRY(ensure_dtag(c, total));
+    a.b.dtag = c->dtag;
+    init_dtag_kernel<<<blocks_for(total), 256, 0, s>>>(total, c->dtag);
+    NP_CK(cudaGetLastError());
+    seed_dtag_kernel<<<blocks_for(nsrc), 256, 0, s>>>(c->w.st, c->ids, nsrc, c->dtag, a.fr0, g->n + 2);
+  } else {
+    fill_unreached_kernel<<<blocks_for(total), 256, 0, s>>>(kind, total, level, dist, a.b.stamp);
+    NP_CK(cudaGetLastError());
+    seed_sources_kernel<<<blocks_for(nsrc), 256, 0, s>>>(c->w.st, kind, c->ids, nsrc, level, dist, a.fr0, g->n + 2);
+  }
   NP_CK(cudaGetLastError());
   c->e.prof_next_parents = nsrc;
   NP_TRY(run_levels(c->e, c->w, p, a, *cfg, total, g->n + 2, s));
+  if (kind == 1) {
+    dtag_to_dist_kernel<<<blocks_for(total), 256, 0, s>>>(total, c->dtag, dist);
+    NP_CK(cudaGetLastError());
+  }
   return finish(c->e, c->w, s, stats);
 }
 
@@ -242,6 +281,7 @@ np_status np_destroy(np_ctx* c) {
   if (c->stage) cudaFree(c->stage);
   if (c->ids) cudaFree(c->ids);
   if (c->tri) cudaFree(c->tri);
+  if (c->dtag) cudaFree(c->dtag);
   engine_release(c->e);
   delete c;
   return NP_OK;

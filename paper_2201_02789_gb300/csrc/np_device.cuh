@@ -41,6 +41,12 @@
 #ifndef NP_SERIAL_BATCH
 #define NP_SERIAL_BATCH 8
 #endif
+// 1: a relaxation reads dist(v) first and issues the atomic only when it would
+// lower it; 0: every relaxation issues the atomic (one dependent round trip
+// fewer, more atomics)
+#ifndef NP_SSSP_PRECHECK
+#define NP_SSSP_PRECHECK 1
+#endif
 #ifdef NP_CHILD_MAXREG
 #define NP_CHILD_BOUNDS __maxnreg__(NP_CHILD_MAXREG)
 #define NP_CHILD_AGG_BOUNDS(CF) __maxnreg__(NP_CHILD_MAXREG)
@@ -137,6 +143,7 @@ struct BodyArgs {
   int vmask;
   const int* row_ptr;            // triangle counting: row bounds of a child's vertex
   unsigned long long* acc;       // triangle counting: kTcSlots partial counts
+  unsigned long long* dtag;      // SSSP, packed form: dist << 32 | tag per vertex
 };
 
 struct Args {
@@ -626,6 +633,67 @@ struct TcBody {
       for (int t = 0; t < nw; t++) c += sorted_contains(look, nl, __ldg(&walk[t])) ? 1u : 0u;
     }
     if (c) atomicAdd(&b.acc[blockIdx.x & (kTcSlots - 1)], (unsigned long long)c);
+  }
+};
+
+// SSSP with the distance and the append tag in one 64-bit word per vertex:
+// dtag[v] = dist(v) << 32 | t(v), where t(v) = L + 1 of the last iteration
+// that lowered dist(v) (0 before any). One 64-bit atomicMin of
+// (nd << 32 | L + 1) both relaxes and decides the append: v joins the next
+// frontier iff nd was strictly below the old distance and the old tag was not
+// L + 1 (the first strict improvement of v in this iteration). An equal
+// distance keeps the older, smaller tag, so a later strict improvement in the
+// same iteration still sees whether v was appended. This saves the stamp
+// exchange, one dependent L2 round trip per improving batch.
+struct Sssp64Body {
+  static constexpr bool kOffsets = false;
+  static constexpr bool kPushes = true;
+  static constexpr bool kBalance = false;
+  struct P {
+    int base;
+    unsigned du;
+    int qbase;
+  };
+  struct F {
+    int v;
+    unsigned w;
+  };
+  __device__ static void count(const Args& a, int pid, int& base, int& N) {
+    const int u = pid & a.b.vmask;
+    base = __ldg(&a.row_ptr[u]);
+    N = __ldg(&a.row_ptr[u + 1]) - base;
+  }
+  __device__ static P parent(const BodyArgs& b, int pid, int base, int) {
+    return P{base, (unsigned)(__ldcg(&b.dtag[pid]) >> 32), pid & ~b.vmask};
+  }
+  __device__ static F fetch(const BodyArgs& b, const P& p, int i) {
+    return F{p.qbase | __ldg(&b.col[p.base + i]), __ldg(&b.w[p.base + i])};
+  }
+  template <int K>
+  __device__ static void apply_batch(const BodyArgs& b, const P& p, const int (&)[K], const F (&f)[K],
+                                     const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
+    const bool live = p.du != 0xffffffffu;
+    const unsigned tag = (unsigned)(b.L + 1);
+    unsigned long long nd[K], cur[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      v[k] = f[k].v;
+      const unsigned long long s = (unsigned long long)p.du + f[k].w;
+      nd[k] = ((s >= 0xffffffffull ? 0xfffffffeull : s) << 32) | tag;
+#if NP_SSSP_PRECHECK
+      cur[k] = (valid[k] && live) ? __ldcg(&b.dtag[v[k]]) : 0ull;
+#else
+      cur[k] = 0xffffffffffffffffull;
+#endif
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      push[k] = valid[k] && live && (nd[k] >> 32) < (cur[k] >> 32);
+      if (push[k]) cur[k] = atomicMin(&b.dtag[v[k]], nd[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++)
+      push[k] = push[k] && (nd[k] >> 32) < (cur[k] >> 32) && (unsigned)cur[k] != tag;
   }
 };
 

@@ -134,6 +134,49 @@ __global__ void sum_u64_kernel(const unsigned long long* part, int n, unsigned l
   }
 }
 
+__global__ void init_dtag_kernel(long long total, unsigned long long* dtag) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total; v += stride)
+    dtag[v] = 0xffffffff00000000ull;
+}
+
+__global__ void seed_dtag_kernel(LevelState* st, const int* ids, int nsrc, unsigned long long* dtag, int* fr0,
+                                 int max_levels) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsrc; i += gridDim.x * blockDim.x) {
+    dtag[ids[i]] = 0ull;
+    fr0[i] = ids[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->base = 0;
+    st->count[0] = nsrc;
+    st->count[1] = 0;
+    st->count[2] = 0;
+    st->max_levels = max_levels;
+    reset_slots(st);
+  }
+}
+
+__global__ void init_dtag_solve_kernel(LevelState* st, int n, int src, unsigned long long* dtag, int* fr0,
+                                       int max_levels) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    dtag[v] = v == src ? 0ull : 0xffffffff00000000ull;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    fr0[0] = src;
+    st->base = 0;
+    st->count[0] = 1;
+    st->count[1] = 0;
+    st->count[2] = 0;
+    st->max_levels = max_levels;
+    reset_slots(st);
+  }
+}
+
+__global__ void dtag_to_dist_kernel(long long total, const unsigned long long* dtag, unsigned* dist) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total; v += stride)
+    dist[v] = (unsigned)(dtag[v] >> 32);
+}
+
 // Between graph bodies or chunks: the next body position 0 is level base + K.
 __global__ void advance_base_kernel(LevelState* st, int K) { st->base += K; }
 

@@ -153,6 +153,15 @@ __global__ void fill_unreached_kernel(int kind, long long total, int* level, uns
 __global__ void seed_sources_kernel(LevelState* st, int kind, const int* ids, int nsrc, int* level, unsigned* dist,
                                     int* fr0, int max_levels);
 __global__ void advance_base_kernel(LevelState* st, int K);
+// Packed SSSP state: dtag[0, total) = unreached (all ones << 32), then the
+// sources (ids) at distance 0 become the first frontier; finally dist = dtag >> 32.
+__global__ void init_dtag_kernel(long long total, unsigned long long* dtag);
+__global__ void seed_dtag_kernel(LevelState* st, const int* ids, int nsrc, unsigned long long* dtag, int* fr0,
+                                 int max_levels);
+__global__ void dtag_to_dist_kernel(long long total, const unsigned long long* dtag, unsigned* dist);
+// Single-source start of the packed form in one kernel (as init_solve_kernel).
+__global__ void init_dtag_solve_kernel(LevelState* st, int n, int src, unsigned long long* dtag, int* fr0,
+                                       int max_levels);
 // *out (+)= the sum of part[0, n) (one block)
 __global__ void sum_u64_kernel(const unsigned long long* part, int n, unsigned long long* out, int accumulate);
 // Sets *bad when a CSR breaks its contract: row_ptr[0] != 0, row_ptr[n] != m,

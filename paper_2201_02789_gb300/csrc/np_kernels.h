@@ -28,6 +28,7 @@ struct BodyKernels {
 
 const BodyKernels& bfs_kernels();
 const BodyKernels& sssp_kernels();
+const BodyKernels& sssp64_kernels();
 const BodyKernels& bezier_kernels();
 const BodyKernels& tc_kernels();
 

@@ -47,24 +47,24 @@ __device__ __forceinline__ const int* dctl_busy(const Ctl* c, int S) {
 }
 
 // Resets the arrays of the slots admitted this step (blockIdx.y = admission).
-__global__ void slot_reset_kernel(const Ctl* ctl, int kind, int lg, int* level, unsigned* dist, int* stamp) {
+// SSSP pools keep the packed state (distance << 32 | append tag).
+__global__ void slot_reset_kernel(const Ctl* ctl, int kind, int lg, int* level, unsigned long long* dtag) {
   if ((int)blockIdx.y >= ctl->nadm) return;
   const int slot = dctl_adm(ctl)[blockIdx.y].x;
   const long long base = (long long)slot << lg;
   const int npad = 1 << lg;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < npad; v += gridDim.x * blockDim.x) {
-    if (kind == 0) {
+    if (kind == 0)
       level[base + v] = -1;
-    } else {
-      dist[base + v] = 0xffffffffu;
-      stamp[base + v] = -1;
-    }
+    else
+      dtag[base + v] = 0xffffffff00000000ull;
   }
 }
 
 // Puts the admitted sources into the frontier of the current level.
-__global__ void slot_admit_kernel(LevelState* st, const Ctl* ctl, int kind, int lg, int* level, unsigned* dist,
-                                  int* fr0, int* fr1, unsigned long long* slot_out, int* slot_L0) {
+__global__ void slot_admit_kernel(LevelState* st, const Ctl* ctl, int kind, int lg, int* level,
+                                  unsigned long long* dtag, int* fr0, int* fr1, unsigned long long* slot_out,
+                                  int* slot_L0) {
   __shared__ int c0, L;
   const int nadm = ctl->nadm;
   if (nadm <= 0) return;
@@ -80,7 +80,7 @@ __global__ void slot_admit_kernel(LevelState* st, const Ctl* ctl, int kind, int 
     if (kind == 0)
       level[id] = L;
     else
-      dist[id] = 0u;
+      dtag[id] = 0ull;
     fr[c0 + i] = id;
     slot_out[a.x] = ((unsigned long long)(unsigned)a.w << 32) | (unsigned)a.z;
     slot_L0[a.x] = L;
@@ -108,8 +108,8 @@ __global__ void slot_histogram_kernel(const LevelState* st, const int* fr0, cons
 
 // Copies every resident slot with no frontier entries left to its caller's array.
 __global__ void slot_retire_kernel(const Ctl* ctl, int S, const int* active, int kind, int lg, int n,
-                                   const int* level, const unsigned* dist, const unsigned long long* slot_out,
-                                   const int* slot_L0) {
+                                   const int* level, const unsigned long long* dtag,
+                                   const unsigned long long* slot_out, const int* slot_L0) {
   const int slot = blockIdx.y;
   if (!dctl_busy(ctl, S)[slot] || __ldcg(&active[slot]) != 0) return;
   const long long base = (long long)slot << lg;
@@ -119,7 +119,7 @@ __global__ void slot_retire_kernel(const Ctl* ctl, int S, const int* active, int
       const int l = level[base + v];
       reinterpret_cast<int*>(slot_out[slot])[v] = l >= 0 ? l - L0 : -1;
     } else {
-      reinterpret_cast<unsigned*>(slot_out[slot])[v] = dist[base + v];
+      reinterpret_cast<unsigned*>(slot_out[slot])[v] = (unsigned)(dtag[base + v] >> 32);
     }
   }
 }
@@ -141,7 +141,7 @@ struct Pool {
   Workspace ws;
   unsigned char* mem = nullptr;   // state | ctl | slot_out | slot_L0 | active
   int* level = nullptr;
-  unsigned* dist = nullptr;
+  unsigned long long* dtag = nullptr;
   Ctl* d_ctl = nullptr;
   unsigned long long* slot_out = nullptr;
   int* slot_L0 = nullptr;
@@ -163,9 +163,8 @@ int ceil_log2(int n) {
 }
 
 size_t pool_state_bytes(int kind, int lg, int S) {
-  (void)kind;
   const size_t elems = (size_t)S << lg;
-  return align_up(sizeof(int) * elems) + align_up(ctl_bytes(S)) + align_up(sizeof(unsigned long long) * S) +
+  return align_up((kind == 0 ? sizeof(int) : sizeof(unsigned long long)) * elems) + align_up(ctl_bytes(S)) + align_up(sizeof(unsigned long long) * S) +
          align_up(sizeof(int) * S) + align_up(sizeof(int) * (S + 1));
 }
 
@@ -190,7 +189,7 @@ namespace {
 
 np_status build_pool_graph(np_server* sv, Pool& p) {
   Engine& e = sv->e;
-  const BodyKernels& K = p.kind == 0 ? bfs_kernels() : sssp_kernels();
+  const BodyKernels& K = p.kind == 0 ? bfs_kernels() : sssp64_kernels();
   Plan plan = make_plan(K, p.cfg);
   Args a;
   base_args(p.ws, p.cfg, a);
@@ -198,7 +197,7 @@ np_status build_pool_graph(np_server* sv, Pool& p) {
   a.b.col = p.g.col_idx;
   a.b.w = p.g.weights;
   a.b.level = p.level;
-  a.b.dist = p.dist;
+  a.b.dtag = p.dtag;
   a.b.stamp = wsp<int>(p.ws, p.ws.lay.off_stamp);
   a.b.vmask = (1 << p.lg) - 1;
   const int64_t elems = (int64_t)p.S << p.lg;
@@ -209,8 +208,8 @@ np_status build_pool_graph(np_server* sv, Pool& p) {
   cudaError_t ce = cudaMemcpyAsync(p.d_ctl, p.h_ctl, ctl_bytes(p.S), cudaMemcpyHostToDevice, cs);
   if (ce == cudaSuccess) {
     const int bx = blocks_for(1ll << p.lg, 256, 64);
-    slot_reset_kernel<<<dim3(bx, p.S), 256, 0, cs>>>(p.d_ctl, p.kind, p.lg, p.level, p.dist, a.b.stamp);
-    slot_admit_kernel<<<1, 256, 0, cs>>>(p.ws.st, p.d_ctl, p.kind, p.lg, p.level, p.dist, a.fr0, a.fr1, p.slot_out,
+    slot_reset_kernel<<<dim3(bx, p.S), 256, 0, cs>>>(p.d_ctl, p.kind, p.lg, p.level, p.dtag);
+    slot_admit_kernel<<<1, 256, 0, cs>>>(p.ws.st, p.d_ctl, p.kind, p.lg, p.level, p.dtag, a.fr0, a.fr1, p.slot_out,
                                          p.slot_L0);
     ce = cudaGetLastError();
   }
@@ -223,7 +222,7 @@ np_status build_pool_graph(np_server* sv, Pool& p) {
     slot_histogram_kernel<<<std::max(1, std::min(e.sms * 2, blocks_for(elems))), 256, 0, cs>>>(
         p.ws.st, a.fr0, a.fr1, p.lg, p.S, p.active);
     const int bx = blocks_for(p.n, 256, 64);
-    slot_retire_kernel<<<dim3(bx, p.S), 256, 0, cs>>>(p.d_ctl, p.S, p.active, p.kind, p.lg, p.n, p.level, p.dist,
+    slot_retire_kernel<<<dim3(bx, p.S), 256, 0, cs>>>(p.d_ctl, p.S, p.active, p.kind, p.lg, p.n, p.level, p.dtag,
                                                        p.slot_out, p.slot_L0);
     ce = cudaGetLastError();
   }
@@ -264,7 +263,7 @@ np_status init_pool(np_server* sv, Pool& p) {
   NP_TRY(ws_init(p.ws));
   const int64_t elems = (int64_t)p.S << p.lg;
   NP_TRY(ws_ensure(p.ws, elems));
-  const size_t b_state = align_up(sizeof(int) * (size_t)elems);
+  const size_t b_state = align_up((p.kind == 0 ? sizeof(int) : sizeof(unsigned long long)) * (size_t)elems);
   const size_t b_ctl = align_up(ctl_bytes(p.S));
   const size_t b_out = align_up(sizeof(unsigned long long) * p.S);
   const size_t b_l0 = align_up(sizeof(int) * p.S);
@@ -272,7 +271,7 @@ np_status init_pool(np_server* sv, Pool& p) {
   NP_CK(cudaMalloc(&p.mem, b_state + b_ctl + b_out + b_l0 + b_act));
   NP_CK(cudaMemset(p.mem, 0, b_state + b_ctl + b_out + b_l0 + b_act));
   p.level = p.kind == 0 ? reinterpret_cast<int*>(p.mem) : nullptr;
-  p.dist = p.kind == 1 ? reinterpret_cast<unsigned*>(p.mem) : nullptr;
+  p.dtag = p.kind == 1 ? reinterpret_cast<unsigned long long*>(p.mem) : nullptr;
   p.d_ctl = reinterpret_cast<Ctl*>(p.mem + b_state);
   p.slot_out = reinterpret_cast<unsigned long long*>(p.mem + b_state + b_ctl);
   p.slot_L0 = reinterpret_cast<int*>(p.mem + b_state + b_ctl + b_out);
@@ -284,7 +283,7 @@ np_status init_pool(np_server* sv, Pool& p) {
   NP_CK(cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking));
   p.slot_query.assign((size_t)p.S, -1);
   // empty pool: level 0, no parents, max_levels unbounded
-  seed_sources_kernel<<<1, 32, 0, p.stream>>>(p.ws.st, p.kind, nullptr, 0, p.level, p.dist,
+  seed_sources_kernel<<<1, 32, 0, p.stream>>>(p.ws.st, p.kind, nullptr, 0, p.level, nullptr,
                                               wsp<int>(p.ws, p.ws.lay.off_fr0), INT_MAX - 64);
   NP_CK(cudaGetLastError());
   NP_CK(cudaStreamSynchronize(p.stream));

@@ -1,0 +1,9 @@
+// Kernels of the packed-distance SSSP child body (see np_device.cuh).
+#include "np_table.cuh"
+
+namespace nestpar {
+const BodyKernels& sssp64_kernels() {
+  static const BodyKernels t = make_table<Sssp64Body>();
+  return t;
+}
+}  // namespace nestpar
