@@ -444,6 +444,18 @@ np_status np_bezier_host(np_ctx *ctx, const float *ctrl_host, int32_t ncurves, i
                          float *points_host, int64_t cap, const np_config *cfg, void *stream,
                          np_stats *stats);
 
+/* Checks the bounded device-side waits: runs one wait on a flag that nothing
+ * sets and returns the status it ends with, which must be NP_ERR_TIMEOUT (the
+ * error word is cleared afterwards and the context stays usable).
+ *   which = 0: a decoupled look-back (Section V-A's multi-block scan) whose
+ *              predecessor tile never publishes; gives up after its poll limit
+ *              (about a second); limit_ns is ignored.
+ *   which = 1: the persistent level loop's grid barrier, launched
+ *              cooperatively with two CTAs of which one never arrives; gives up
+ *              after limit_ns (1 ms .. 10 s).
+ * Nothing faults, traps or hangs. */
+np_status np_selftest_wait(np_ctx *ctx, int32_t which, int64_t limit_ns, void *stream);
+
 const char *np_status_string(np_status s);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int32_t np_version(void);

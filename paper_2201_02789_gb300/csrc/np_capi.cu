@@ -511,6 +511,32 @@ np_status np_sssp_host(np_ctx* c, int32_t n, int64_t m, const int32_t* row_ptr_h
   return np_sync(c, stream, stats ? stats : &tmp);
 }
 
+np_status np_selftest_wait(np_ctx* c, int32_t which, int64_t limit_ns, void* stream) {
+  if (!c || which < 0 || which > 1) return NP_ERR_INVALID;
+  if (which == 1 && (limit_ns < 1000000 || limit_ns > 10000000000ll)) return NP_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  NP_CK(cudaSetDevice(c->e.device));
+  cudaStream_t s = (cudaStream_t)stream;
+  NP_TRY(ws_ensure(c->w, 4096));
+  if (which == 0) {
+    np_config cfg;
+    np_config_default(&cfg);
+    Args a;
+    base_args(c->w, cfg, a);
+    selftest_lookback_kernel<<<1, 32, 0, s>>>(a);
+    NP_CK(cudaGetLastError());
+  } else {
+    LevelState* st = c->w.st;
+    NP_CK(cudaMemsetAsync(&st->bar_count, 0, sizeof(unsigned), s));   // no stale arrivals
+    unsigned long long lim = (unsigned long long)limit_ns;
+    void* args[] = {&st, &lim};
+    NP_CK(cudaLaunchCooperativeKernel((const void*)selftest_barrier_kernel, dim3(2), dim3(32), args, 0, s));
+    // the next solve resets the barrier's arrival count (it is left at one)
+  }
+  np_stats tmp;
+  return finish(c->e, c->w, s, &tmp);
+}
+
 np_status np_profile_enable(np_ctx* c, int32_t on) {
   if (!c) return NP_ERR_INVALID;
   std::lock_guard<std::mutex> lk(c->mu);

@@ -1388,7 +1388,7 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 }
 
 // Returns false (in every thread of the CTA) once any CTA has timed out.
-__device__ __forceinline__ bool grid_barrier(LevelState* st, int* s_ok) {
+__device__ __forceinline__ bool grid_barrier(LevelState* st, int* s_ok, unsigned long long limit_ns = kBarrierNs) {
   __syncthreads();
   if (threadIdx.x == 0) {
     bool ok = true;
@@ -1403,7 +1403,7 @@ __device__ __forceinline__ bool grid_barrier(LevelState* st, int* s_ok) {
       unsigned polls = 0;
       while (ld_acquire_u32(&st->bar_gen) == gen) {
         if ((++polls & 63u) == 0u) {
-          if (globaltimer_ns() - t0 > kBarrierNs || (__ldcg(&st->error) & kErrTimeout)) {
+          if (globaltimer_ns() - t0 > limit_ns || (__ldcg(&st->error) & kErrTimeout)) {
             atomicOr(&st->error, kErrTimeout);
             ok = false;
             break;

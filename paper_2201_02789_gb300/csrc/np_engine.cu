@@ -177,6 +177,22 @@ __global__ void dtag_to_dist_kernel(long long total, const unsigned long long* d
     dist[v] = (unsigned)(dtag[v] >> 32);
 }
 
+// Checks of the bounded waits (np_selftest_wait): each waits on a flag that
+// nothing sets and must give up with the timeout bit set.
+// A decoupled look-back for tile 1 of a scan whose tile 0 never publishes
+// (an epoch no solve reaches).
+__global__ void selftest_lookback_kernel(Args a) {
+  const unsigned long long epoch = ((__ldcg(&a.st->solve_id) + (1ull << 28)) << 31) | 7ull;
+  lookback(a.lb_flag, a.lb_agg, a.lb_incl, 1, 0, epoch, V3{1u, 0u, 0u}, a.st);
+}
+
+// A grid barrier that one CTA (blockIdx.x == 1) never reaches.
+__global__ void selftest_barrier_kernel(LevelState* st, unsigned long long limit_ns) {
+  __shared__ int s_ok;
+  if (blockIdx.x == 1) return;
+  grid_barrier(st, &s_ok, limit_ns);
+}
+
 // Between graph bodies or chunks: the next body position 0 is level base + K.
 __global__ void advance_base_kernel(LevelState* st, int K) { st->base += K; }
 

@@ -153,6 +153,9 @@ __global__ void fill_unreached_kernel(int kind, long long total, int* level, uns
 __global__ void seed_sources_kernel(LevelState* st, int kind, const int* ids, int nsrc, int* level, unsigned* dist,
                                     int* fr0, int max_levels);
 __global__ void advance_base_kernel(LevelState* st, int K);
+// Bounded-wait checks of np_selftest_wait (each waits on a flag nothing sets).
+__global__ void selftest_lookback_kernel(Args a);
+__global__ void selftest_barrier_kernel(LevelState* st, unsigned long long limit_ns);
 // Packed SSSP state: dtag[0, total) = unreached (all ones << 32), then the
 // sources (ids) at distance 0 become the first frontier; finally dist = dtag >> 32.
 __global__ void init_dtag_kernel(long long total, unsigned long long* dtag);

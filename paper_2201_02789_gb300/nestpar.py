@@ -183,6 +183,7 @@ _SIGS = {
     "np_server_poll": [_VP, _I64, ctypes.POINTER(np_query_info)],
     "np_server_finished": [_VP, _VP, _I32, ctypes.POINTER(ctypes.c_int32)],
     "np_triangles": [_VP, ctypes.POINTER(np_csr), _VP, ctypes.POINTER(np_config), _VP, ctypes.POINTER(np_stats)],
+    "np_selftest_wait": [_VP, _I32, _I64, _VP],
     "np_status_string": [_I32],
     "np_version": [],
 }
@@ -515,6 +516,11 @@ def np_server_finished(sv, max_count: int = 4096) -> list[int]:
     k = ctypes.c_int32()
     _check(lib().np_server_finished(sv, buf.ctypes.data, int(max_count), ctypes.byref(k)), "np_server_finished", True)
     return buf[:k.value].tolist()
+
+
+def np_selftest_wait(ctx, which: int, limit_ns: int = 0, stream=None) -> int:
+    """Status of one bounded wait on a flag nothing sets (expected NP_ERR_TIMEOUT)."""
+    return int(lib().np_selftest_wait(ctx, int(which), int(limit_ns), _stream(stream)))
 
 
 def config(form: str = "tca", **kw) -> np_config:

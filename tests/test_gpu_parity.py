@@ -402,3 +402,21 @@ def test_multiblock_repeated_runs(ctx, scan):
                              threshold=[8, 32, 128][rep % 3], child_block=[32, 256][gi])
             np.testing.assert_array_equal(bfs(ctx, dg, 0, cfg), rl)
             np.testing.assert_array_equal(sssp(ctx, dg, 0, cfg), rd)
+
+
+# ------------------------------------------------------------ bounded waits
+
+@pytest.mark.parametrize("which,limit_ns", [(0, 0), (1, 50_000_000)])
+def test_bounded_waits_time_out_and_context_survives(ctx, g4k, which, limit_ns):
+    """A look-back whose predecessor never publishes, and a grid barrier one CTA never
+    reaches, both give up with NP_ERR_TIMEOUT; the next solve on the context is exact."""
+    import time
+    g, dg, ref_l, ref_d = g4k
+    t = time.perf_counter()
+    assert npb.np_selftest_wait(ctx.handle, which, limit_ns) == npb.NP_ERR_TIMEOUT
+    assert time.perf_counter() - t < 30.0
+    np.testing.assert_array_equal(bfs(ctx, dg, 0, npb.config("tca")), ref_l)
+    cfg = npb.config("tca", driver=npb.NP_DRIVER_PERSISTENT)
+    d, st = sssp(ctx, dg, 0, cfg, stats=True)
+    np.testing.assert_array_equal(d, ref_d)
+    assert st["error"] == 0
