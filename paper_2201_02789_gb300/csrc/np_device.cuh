@@ -41,6 +41,10 @@
 #ifndef NP_SERIAL_BATCH
 #define NP_SERIAL_BATCH 8
 #endif
+// items per lane per round of the aggregated form's spread serial loop
+#ifndef NP_SPREAD_BATCH
+#define NP_SPREAD_BATCH 8
+#endif
 // 1: a relaxation reads dist(v) first and issues the atomic only when it would
 // lower it; 0: every relaxation issues the atomic (one dependent round trip
 // fewer, more atomics)
@@ -505,9 +509,12 @@ struct BfsBody {
     N = __ldg(&a.row_ptr[u + 1]) - base;
   }
   __device__ static P parent(const BodyArgs& b, int pid, int base, int) { return P{base, pid & ~b.vmask}; }
+  __device__ static P shfl(const P& p, int src) {
+    return P{__shfl_sync(kFull, p.base, src), __shfl_sync(kFull, p.qbase, src)};
+  }
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) { return F{p.qbase | __ldg(&b.col[p.base + i])}; }
   template <int K>
-  __device__ static void apply_batch(const BodyArgs& b, const P&, const int (&)[K], const F (&f)[K],
+  __device__ static void apply_batch(const BodyArgs& b, const P (&)[K], const int (&)[K], const F (&f)[K],
                                      const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
     int cur[K];
 #pragma unroll
@@ -550,21 +557,26 @@ struct SsspBody {
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) {
     return F{p.qbase | __ldg(&b.col[p.base + i]), __ldg(&b.w[p.base + i])};
   }
+  __device__ static P shfl(const P& p, int src) {
+    return P{__shfl_sync(kFull, p.base, src), (unsigned)__shfl_sync(kFull, (int)p.du, src),
+             __shfl_sync(kFull, p.qbase, src)};
+  }
   template <int K>
-  __device__ static void apply_batch(const BodyArgs& b, const P& p, const int (&)[K], const F (&f)[K],
+  __device__ static void apply_batch(const BodyArgs& b, const P (&p)[K], const int (&)[K], const F (&f)[K],
                                      const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
-    const bool live = p.du != 0xffffffffu;
     unsigned nd[K], cur[K];
+    bool live[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
       v[k] = f[k].v;
-      const unsigned long long s = (unsigned long long)p.du + f[k].w;
+      live[k] = p[k].du != 0xffffffffu;
+      const unsigned long long s = (unsigned long long)p[k].du + f[k].w;
       nd[k] = s >= 0xffffffffull ? 0xfffffffeu : (unsigned)s;
-      cur[k] = (valid[k] && live) ? __ldcg(&b.dist[v[k]]) : 0u;
+      cur[k] = (valid[k] && live[k]) ? __ldcg(&b.dist[v[k]]) : 0u;
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {
-      push[k] = valid[k] && live && nd[k] < cur[k];
+      push[k] = valid[k] && live[k] && nd[k] < cur[k];
       if (push[k]) cur[k] = atomicMin(&b.dist[v[k]], nd[k]);
     }
 #pragma unroll
@@ -609,9 +621,12 @@ struct TcBody {
     N = __ldg(&a.row_ptr[pid + 1]) - base;
   }
   __device__ static P parent(const BodyArgs&, int, int base, int N) { return P{base, N}; }
+  __device__ static P shfl(const P& p, int src) {
+    return P{__shfl_sync(kFull, p.base, src), __shfl_sync(kFull, p.n, src)};
+  }
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) { return F{__ldg(&b.col[p.base + i])}; }
   template <int K>
-  __device__ static void apply_batch(const BodyArgs& b, const P& p, const int (&)[K], const F (&f)[K],
+  __device__ static void apply_batch(const BodyArgs& b, const P (&p)[K], const int (&)[K], const F (&f)[K],
                                      const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
     int vb[K], vn[K];
 #pragma unroll
@@ -622,14 +637,14 @@ struct TcBody {
       vn[k] = valid[k] ? __ldg(&b.row_ptr[f[k].v + 1]) - vb[k] : 0;
     }
     unsigned c = 0;
-    const int* nu = b.col + p.base;
 #pragma unroll
     for (int k = 0; k < K; k++) {
+      const int* nu = b.col + p[k].base;
       const int* nv = b.col + vb[k];
-      const bool walk_u = p.n <= vn[k];
+      const bool walk_u = p[k].n <= vn[k];
       const int* walk = walk_u ? nu : nv;
       const int* look = walk_u ? nv : nu;
-      const int nw = walk_u ? p.n : vn[k], nl = walk_u ? vn[k] : p.n;
+      const int nw = walk_u ? p[k].n : vn[k], nl = walk_u ? vn[k] : p[k].n;
       for (int t = 0; t < nw; t++) c += sorted_contains(look, nl, __ldg(&walk[t])) ? 1u : 0u;
     }
     if (c) atomicAdd(&b.acc[blockIdx.x & (kTcSlots - 1)], (unsigned long long)c);
@@ -669,26 +684,31 @@ struct Sssp64Body {
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) {
     return F{p.qbase | __ldg(&b.col[p.base + i]), __ldg(&b.w[p.base + i])};
   }
+  __device__ static P shfl(const P& p, int src) {
+    return P{__shfl_sync(kFull, p.base, src), (unsigned)__shfl_sync(kFull, (int)p.du, src),
+             __shfl_sync(kFull, p.qbase, src)};
+  }
   template <int K>
-  __device__ static void apply_batch(const BodyArgs& b, const P& p, const int (&)[K], const F (&f)[K],
+  __device__ static void apply_batch(const BodyArgs& b, const P (&p)[K], const int (&)[K], const F (&f)[K],
                                      const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
-    const bool live = p.du != 0xffffffffu;
     const unsigned tag = (unsigned)(b.L + 1);
     unsigned long long nd[K], cur[K];
+    bool live[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
       v[k] = f[k].v;
-      const unsigned long long s = (unsigned long long)p.du + f[k].w;
+      live[k] = p[k].du != 0xffffffffu;
+      const unsigned long long s = (unsigned long long)p[k].du + f[k].w;
       nd[k] = ((s >= 0xffffffffull ? 0xfffffffeull : s) << 32) | tag;
 #if NP_SSSP_PRECHECK
-      cur[k] = (valid[k] && live) ? __ldcg(&b.dtag[v[k]]) : 0ull;
+      cur[k] = (valid[k] && live[k]) ? __ldcg(&b.dtag[v[k]]) : 0ull;
 #else
       cur[k] = 0xffffffffffffffffull;
 #endif
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {
-      push[k] = valid[k] && live && (nd[k] >> 32) < (cur[k] >> 32);
+      push[k] = valid[k] && live[k] && (nd[k] >> 32) < (cur[k] >> 32);
       if (push[k]) cur[k] = atomicMin(&b.dtag[v[k]], nd[k]);
     }
 #pragma unroll
@@ -773,20 +793,26 @@ struct BezierBody {
     return P{__ldg(c), __ldg(c + 1), __ldg(c + 2), __ldg(c + 3), __ldg(c + 4), __ldg(c + 5), base,
              (float)(N - 1)};
   }
+  __device__ static P shfl(const P& p, int src) {
+    return P{__shfl_sync(kFull, p.x0, src), __shfl_sync(kFull, p.y0, src), __shfl_sync(kFull, p.x1, src),
+             __shfl_sync(kFull, p.y1, src), __shfl_sync(kFull, p.x2, src), __shfl_sync(kFull, p.y2, src),
+             __shfl_sync(kFull, p.base, src), __shfl_sync(kFull, p.denom, src)};
+  }
   __device__ static F fetch(const BodyArgs&, const P&, int) { return F{}; }
   template <int K>
-  __device__ static void apply_batch(const BodyArgs& b, const P& p, const int (&idx)[K], const F (&)[K],
+  __device__ static void apply_batch(const BodyArgs& b, const P (&p)[K], const int (&idx)[K], const F (&)[K],
                                      const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
 #pragma unroll
     for (int k = 0; k < K; k++) {
       push[k] = false;
       v[k] = 0;
       if (!valid[k]) continue;
-      const float t = (float)idx[k] / p.denom;
+      const P& q = p[k];
+      const float t = (float)idx[k] / q.denom;
       const float u = 1.0f - t;
       const float b0 = u * u, b1 = 2.0f * u * t, b2 = t * t;
-      b.points[p.base + idx[k]] =
-          make_float2(b0 * p.x0 + b1 * p.x1 + b2 * p.x2, b0 * p.y0 + b1 * p.y1 + b2 * p.y2);
+      b.points[q.base + idx[k]] =
+          make_float2(b0 * q.x0 + b1 * q.x1 + b2 * q.x2, b0 * q.y0 + b1 * q.y1 + b2 * q.y2);
     }
   }
 };
@@ -814,7 +840,10 @@ __device__ __forceinline__ void run_coarsened(const BodyArgs& b, const typename 
     }
     bool pf[KB];
     int pv[KB];
-    Body::template apply_batch<KB>(b, p, idx, f, v, pf, pv);
+    typename Body::P pk[KB];
+#pragma unroll
+    for (int k = 0; k < KB; k++) pk[k] = p;
+    Body::template apply_batch<KB>(b, pk, idx, f, v, pf, pv);
     if constexpr (Body::kPushes) sink.template push<KB>(pf, pv);
   }
 }
@@ -837,7 +866,10 @@ __device__ __forceinline__ void run_serial(const BodyArgs& b, int pid, int base,
     }
     bool pf[KS];
     int pv[KS];
-    Body::template apply_batch<KS>(b, p, idx, f, v, pf, pv);
+    typename Body::P pk[KS];
+#pragma unroll
+    for (int k = 0; k < KS; k++) pk[k] = p;
+    Body::template apply_batch<KS>(b, pk, idx, f, v, pf, pv);
     if constexpr (Body::kPushes) sink.template push<KS>(pf, pv);
   }
 }
@@ -1312,27 +1344,76 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
         st->agg_blocks[slot] = (int)(x.b + tb);
       }
     }
-    // serialised children, warp-uniform: lane l walks its own parent's
-    // children in order; lanes with fewer (or none) idle through the tail
     const int myN = serial ? N : 0;
-    const int maxN = (int)__reduce_max_sync(kFull, (unsigned)myN);
-    if (maxN > 0) {
-      constexpr int KS = NP_SERIAL_BATCH;
-      const typename Body::P p = Body::parent(b, valid ? pid : 0, base, N);
-      for (int i0 = 0; i0 < maxN; i0 += KS) {
-        typename Body::F f[KS];
-        bool v[KS];
-        int idx[KS];
+    if constexpr (FORM == 1) {
+      // Serialised children of the aggregated form, spread over the warp's
+      // lanes: the tile's below-threshold children are numbered in parent
+      // order, item t goes to lane t % 32, which finds its parent (the first
+      // lane whose inclusive count exceeds t) by a shuffle search and takes
+      // the parent's fields by shuffle. The work stays in the parent kernel,
+      // with every lane busy instead of each lane walking only its own list.
+      int incl = myN;
 #pragma unroll
-        for (int k = 0; k < KS; k++) {
-          idx[k] = i0 + k;
-          v[k] = idx[k] < myN;
-          f[k] = v[k] ? Body::fetch(b, p, idx[k]) : typename Body::F{};
+      for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += x;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      if (total > 0) {
+        constexpr int KS = NP_SPREAD_BATCH;
+        const typename Body::P pm = Body::parent(b, serial ? pid : 0, base, N);
+        const int excl = incl - myN;
+        for (int t0 = 0; t0 < total; t0 += 32 * KS) {
+          typename Body::F f[KS];
+          typename Body::P pk[KS];
+          bool v[KS];
+          int idx[KS];
+#pragma unroll
+          for (int k = 0; k < KS; k++) {
+            const int t = t0 + k * 32 + lane;
+            int j = 0;
+#pragma unroll
+            for (int s2 = 16; s2 > 0; s2 >>= 1) {
+              const int x = __shfl_sync(kFull, incl, j + s2 - 1);
+              if (x <= t) j += s2;
+            }
+            j = j > 31 ? 31 : j;
+            v[k] = t < total;
+            idx[k] = t - __shfl_sync(kFull, excl, j);
+            pk[k] = Body::shfl(pm, j);
+            f[k] = v[k] ? Body::fetch(b, pk[k], idx[k]) : typename Body::F{};
+          }
+          bool pf[KS];
+          int pv[KS];
+          Body::template apply_batch<KS>(b, pk, idx, f, v, pf, pv);
+          if constexpr (Body::kPushes) sink.template push<KS>(pf, pv);
         }
-        bool pf[KS];
-        int pv[KS];
-        Body::template apply_batch<KS>(b, p, idx, f, v, pf, pv);
-        if constexpr (Body::kPushes) sink.template push<KS>(pf, pv);
+      }
+    } else {
+      // No-CDP form (the paper's baseline): lane l walks its own parent's
+      // children in order; lanes with fewer (or none) idle through the tail
+      const int maxN = (int)__reduce_max_sync(kFull, (unsigned)myN);
+      if (maxN > 0) {
+        constexpr int KS = NP_SERIAL_BATCH;
+        const typename Body::P p = Body::parent(b, valid ? pid : 0, base, N);
+        typename Body::P pk[KS];
+#pragma unroll
+        for (int k = 0; k < KS; k++) pk[k] = p;
+        for (int i0 = 0; i0 < maxN; i0 += KS) {
+          typename Body::F f[KS];
+          bool v[KS];
+          int idx[KS];
+#pragma unroll
+          for (int k = 0; k < KS; k++) {
+            idx[k] = i0 + k;
+            v[k] = idx[k] < myN;
+            f[k] = v[k] ? Body::fetch(b, p, idx[k]) : typename Body::F{};
+          }
+          bool pf[KS];
+          int pv[KS];
+          Body::template apply_batch<KS>(b, pk, idx, f, v, pf, pv);
+          if constexpr (Body::kPushes) sink.template push<KS>(pf, pv);
+        }
       }
     }
   }
