@@ -41,6 +41,25 @@
 #ifndef NP_SERIAL_BATCH
 #define NP_SERIAL_BATCH 8
 #endif
+// Programmatic dependent launch between the kernels of the launch-free level
+// loop: each such kernel lets the next one be scheduled at once, then waits
+// for its own predecessor to complete before it reads anything. A kernel
+// without this entry is never launched with the attribute.
+#ifndef NP_PDL
+#define NP_PDL 1
+#endif
+#if NP_PDL
+#define NP_PDL_ENTRY()                          \
+  do {                                          \
+    cudaTriggerProgrammaticLaunchCompletion();  \
+    cudaGridDependencySynchronize();            \
+  } while (0)
+#else
+#define NP_PDL_ENTRY() \
+  do {                 \
+  } while (0)
+#endif
+
 // items per lane per round of the aggregated form's spread serial loop
 #ifndef NP_SPREAD_BATCH
 #define NP_SPREAD_BATCH 8
@@ -999,6 +1018,7 @@ __device__ __forceinline__ void agg_totals(const LevelState* st, int L, int mode
 // totals are read from the level state.
 template <class Body, int CF>
 __global__ void NP_CHILD_AGG_BOUNDS(CF) child_agg(BodyArgs b, AggSeg s) {
+  NP_PDL_ENTRY();
   __shared__ int s_stage[kCtaStage];
   __shared__ int s_stage_n, s_stage_base;
   int nrec = s.nrec, total = s.total;
@@ -1069,6 +1089,9 @@ __device__ __forceinline__ void warp_stat(unsigned* s_stat, int k, unsigned v) {
 // below the threshold come last, so no scan ever waits behind a serial loop.
 template <class Body, int GRAN, int CF>
 __global__ void NP_PARENT_BOUNDS parent_kernel(Args a) {
+  // launched early only as the No-CDP baseline (no launch site); the
+  // device-launch forms complete with their children and are never
+  if constexpr (GRAN == G_NODP) NP_PDL_ENTRY();
   __shared__ int s_tile;
   __shared__ uint2 s_scan[33];
   __shared__ V3 s_v3;
@@ -1429,6 +1452,7 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
 
 template <class Body, int FORM>
 __global__ void NP_PARENT_BOUNDS parent_warp(Args a) {
+  NP_PDL_ENTRY();
   __shared__ int s_stage[kCtaStage];
   __shared__ int s_stage_n, s_stage_base;
   LevelState* st = a.st;

@@ -194,12 +194,16 @@ __global__ void selftest_barrier_kernel(LevelState* st, unsigned long long limit
 }
 
 // Between graph bodies or chunks: the next body position 0 is level base + K.
-__global__ void advance_base_kernel(LevelState* st, int K) { st->base += K; }
+__global__ void advance_base_kernel(LevelState* st, int K) {
+  NP_PDL_ENTRY();
+  st->base += K;
+}
 
 // End of a conditional-while body of K levels: move base on and continue while
 // the next level has parents. The iteration cap turns a level loop that failed
 // to terminate into an error instead of an endless loop.
 __global__ void set_cond_kernel(LevelState* st, cudaGraphConditionalHandle h, int K) {
+  NP_PDL_ENTRY();
   const int L = st->base + K;
   st->base = L;
   const int c = st->count[L % 3];
@@ -415,6 +419,25 @@ int resolve_driver(const Plan& p, const np_config& cfg) {
 
 namespace {
 
+// A launch that may be scheduled while its predecessor on the stream is still
+// running (programmatic dependent launch); the kernel waits for it itself.
+cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, void** args, cudaStream_t s, bool pdl) {
+  if (!pdl) return cudaLaunchKernel(fn, grid, block, args, 0, s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+constexpr bool kPdl = NP_PDL != 0;
+
 AggSeg make_seg(const Args& a, const Grids& g, bool level_mode) {
   AggSeg seg{};
   seg.rec = a.rec;
@@ -444,20 +467,23 @@ BodyArgs child_body(const Args& a, bool level_mode) {
 // fixed pass.
 np_status enqueue_pass(const Plan& p, Args a, const Grids& g, bool level_mode, int k, cudaStream_t s) {
   a.k = level_mode ? k : 0;
+  // device-launch forms must complete with their children: no early launch
+  const bool pdl = kPdl && p.mode != M_DEVICE_LAUNCH;
   void* pargs[] = {&a};
-  NP_CK(cudaLaunchKernel(p.parent, dim3(g.pgrid), dim3(g.pblock), pargs, 0, s));
+  NP_CK(launch_pdl(p.parent, dim3(g.pgrid), dim3(g.pblock), pargs, s, pdl));
   if (p.mode == M_GRID_HOST) {
     AggSeg seg = make_seg(a, g, level_mode);
     BodyArgs b = child_body(a, level_mode);
     void* cargs[] = {&b, &seg};
-    NP_CK(cudaLaunchKernel(p.child, dim3(g.cgrid), dim3(g.cthreads), cargs, 0, s));
+    NP_CK(launch_pdl(p.child, dim3(g.cgrid), dim3(g.cthreads), cargs, s, pdl));
   }
   return NP_OK;
 }
 
-np_status enqueue_advance(LevelState* st, int K, cudaStream_t s) {
-  advance_base_kernel<<<1, 1, 0, s>>>(st, K);
-  NP_CK(cudaGetLastError());
+np_status enqueue_advance(LevelState* st, int K, cudaStream_t s, bool after_launch_free) {
+  // after a device-launch form it must wait for the level's children: no early launch
+  void* args[] = {&st, &K};
+  NP_CK(launch_pdl((const void*)advance_base_kernel, dim3(1), dim3(1), args, s, kPdl && after_launch_free));
   return NP_OK;
 }
 
@@ -557,7 +583,7 @@ np_status chunk_graph(Engine& e, Workspace& w, const Plan& p, const Args& a, con
   NP_CK(cudaStreamBeginCapture(e.cap_stream, cudaStreamCaptureModeThreadLocal));
   np_status st = NP_OK;
   for (int k = 0; k < K && st == NP_OK; k++) st = enqueue_pass(p, a, g, true, k, e.cap_stream);
-  if (st == NP_OK) st = enqueue_advance(w.st, K, e.cap_stream);
+  if (st == NP_OK) st = enqueue_advance(w.st, K, e.cap_stream, p.mode != M_DEVICE_LAUNCH);
   cudaGraph_t graph = nullptr;
   cudaError_t ce = cudaStreamEndCapture(e.cap_stream, &graph);
   if (st != NP_OK) {
@@ -582,8 +608,8 @@ np_status add_while_node(Engine& e, LevelState* st, cudaGraph_t graph, const cud
   NP_CK(cudaStreamBeginCaptureToGraph(e.cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   np_status s = NP_OK;
   for (int k = 0; k < K && s == NP_OK; k++) s = enqueue_pass(p, a, g, true, k, e.cap_stream);
-  set_cond_kernel<<<1, 1, 0, e.cap_stream>>>(st, h, K);
-  cudaError_t le = cudaGetLastError();
+  void* cargs[] = {&st, &h, &K};
+  cudaError_t le = launch_pdl((const void*)set_cond_kernel, dim3(1), dim3(1), cargs, e.cap_stream, kPdl);
   cudaError_t ce = cudaStreamEndCapture(e.cap_stream, &body);
   if (s != NP_OK) return s;
   NP_CK(le);
@@ -700,7 +726,7 @@ np_status run_levels(Engine& e, Workspace& w, const Plan& p, const Args& a, cons
       NP_CK(cudaGraphLaunch(exec, s));
     } else {
       for (int k = 0; k < K; k++) NP_TRY(enqueue_pass(p, a, g, true, k, s));
-      NP_TRY(enqueue_advance(w.st, K, s));
+      NP_TRY(enqueue_advance(w.st, K, s, p.mode != M_DEVICE_LAUNCH));
     }
     int level = 0, count = 0;
     NP_TRY(read_header(e, w, s, &level, &count));

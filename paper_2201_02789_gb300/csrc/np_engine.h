@@ -114,7 +114,7 @@ Grids grids_for(Engine& e, const Plan& p, const np_config& cfg, int64_t max_pare
 int resolve_driver(const Plan& p, const np_config& cfg);
 
 np_status enqueue_pass(const Plan& p, Args a, const Grids& g, bool level_mode, int k, cudaStream_t s);
-np_status enqueue_advance(LevelState* st, int K, cudaStream_t s);
+np_status enqueue_advance(LevelState* st, int K, cudaStream_t s, bool after_launch_free = false);
 np_status profiled_pass(Engine& e, const Workspace& w, const Plan& p, Args a, const Grids& g, bool level_mode,
                         cudaStream_t s);
 

@@ -215,7 +215,7 @@ np_status build_pool_graph(np_server* sv, Pool& p) {
   }
   if (ce == cudaSuccess) {
     for (int k = 0; k < sv->levels_per_step && st == NP_OK; k++) st = enqueue_pass(plan, a, gr, true, k, cs);
-    if (st == NP_OK) st = enqueue_advance(p.ws.st, sv->levels_per_step, cs);
+    if (st == NP_OK) st = enqueue_advance(p.ws.st, sv->levels_per_step, cs, true);
   }
   if (ce == cudaSuccess && st == NP_OK) ce = cudaMemsetAsync(p.active, 0, sizeof(int) * (size_t)(p.S + 1), cs);
   if (ce == cudaSuccess && st == NP_OK) {
