@@ -48,6 +48,7 @@
 #ifndef NP_PDL
 #define NP_PDL 1
 #endif
+
 #if NP_PDL
 #define NP_PDL_ENTRY()                          \
   do {                                          \
@@ -1352,7 +1353,8 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
       V3 x{0u, 0u, 0u};
       if (a.scan == 0) {
         x = lookback(a.lb_flag, a.lb_agg, a.lb_incl, tile, 0, epoch, V3{ta, tb, 0u}, st);
-      } else {
+      } else if (ta > 0) {
+        // (a tile without launching parents needs no slots: no atomic round trip)
         unsigned long long old = 0ull;
         if (lane == 0) old = atomicAdd(&st->agg_acc[slot], ((unsigned long long)ta << 40) | tb);
         old = __shfl_sync(kFull, old, 0);
