@@ -35,6 +35,11 @@
 
 // Tuning knobs (compile time): items a child thread keeps in flight, items a
 // serialising parent thread keeps in flight, optional register caps.
+// 1: aggregated child blocks stage their edge lists in shared memory with the
+// bulk-copy engine, one block ahead (bodies with contiguous lists, CF <= 8)
+#ifndef NP_TMA_STAGE
+#define NP_TMA_STAGE 0
+#endif
 #ifndef NP_CHILD_BATCH
 #define NP_CHILD_BATCH 8
 #endif
@@ -516,6 +521,7 @@ struct BfsBody {
   static constexpr bool kOffsets = false;
   static constexpr bool kPushes = true;
   static constexpr bool kBalance = false;   // child blocks cost the same: static ranges
+  static constexpr int kStage = 1;          // edge lists the child can stage: col
   struct P {
     int base;
     int qbase;   // query part of the ids of this parent's children
@@ -533,6 +539,7 @@ struct BfsBody {
     return P{__shfl_sync(kFull, p.base, src), __shfl_sync(kFull, p.qbase, src)};
   }
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) { return F{p.qbase | __ldg(&b.col[p.base + i])}; }
+  __device__ static F fetch_from(const P& p, int col, unsigned) { return F{p.qbase | col}; }
   template <int K>
   __device__ static void apply_batch(const BodyArgs& b, const P (&)[K], const int (&)[K], const F (&f)[K],
                                      const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
@@ -557,6 +564,7 @@ struct SsspBody {
   static constexpr bool kOffsets = false;
   static constexpr bool kPushes = true;
   static constexpr bool kBalance = false;
+  static constexpr int kStage = 2;          // col and w
   struct P {
     int base;
     unsigned du;
@@ -577,6 +585,7 @@ struct SsspBody {
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) {
     return F{p.qbase | __ldg(&b.col[p.base + i]), __ldg(&b.w[p.base + i])};
   }
+  __device__ static F fetch_from(const P& p, int col, unsigned w) { return F{p.qbase | col, w}; }
   __device__ static P shfl(const P& p, int src) {
     return P{__shfl_sync(kFull, p.base, src), (unsigned)__shfl_sync(kFull, (int)p.du, src),
              __shfl_sync(kFull, p.qbase, src)};
@@ -629,6 +638,7 @@ struct TcBody {
   static constexpr bool kOffsets = false;
   static constexpr bool kPushes = false;
   static constexpr bool kBalance = true;    // block cost varies with the lists' lengths
+  static constexpr int kStage = 0;
   struct P {
     int base;
     int n;
@@ -684,6 +694,7 @@ struct Sssp64Body {
   static constexpr bool kOffsets = false;
   static constexpr bool kPushes = true;
   static constexpr bool kBalance = false;
+  static constexpr int kStage = 2;          // col and w
   struct P {
     int base;
     unsigned du;
@@ -704,6 +715,7 @@ struct Sssp64Body {
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) {
     return F{p.qbase | __ldg(&b.col[p.base + i]), __ldg(&b.w[p.base + i])};
   }
+  __device__ static F fetch_from(const P& p, int col, unsigned w) { return F{p.qbase | col, w}; }
   __device__ static P shfl(const P& p, int src) {
     return P{__shfl_sync(kFull, p.base, src), (unsigned)__shfl_sync(kFull, (int)p.du, src),
              __shfl_sync(kFull, p.qbase, src)};
@@ -742,6 +754,7 @@ struct BezierBody {
   static constexpr bool kOffsets = true;
   static constexpr bool kPushes = false;
   static constexpr bool kBalance = false;
+  static constexpr int kStage = 0;
   struct P {
     float x0, y0, x1, y1, x2, y2;
     int base;
@@ -942,6 +955,194 @@ __device__ __forceinline__ void child_agg_balanced(const BodyArgs& b, const int4
   if (stid == 0 && done) add_stat(b.st, S_CBLOCKS, (unsigned long long)done);
 }
 
+// ------------------------------------------- TMA-staged aggregated child blocks
+//
+// The edge lists of an aggregated child block (cb * CF consecutive items of
+// one parent) are contiguous, so one elected thread per child block copies
+// them into shared memory with the bulk-copy engine (cp.async.bulk into an
+// mbarrier), one block ahead: the copy of block B + 1 runs while block B does
+// its distance loads and atomics, taking the edge-list round trip off each
+// block's dependent chain. Only the 16-byte aligned interior of a block's
+// range is copied (the copy engine needs 16-byte aligned addresses and sizes);
+// the up to three items at either end are read directly. Every mbarrier wait
+// is bounded in time.
+constexpr int kTmaItems = 256;   // items of one staged child block at most (cb * CF)
+constexpr int kTmaSubs = 8;      // staged child blocks per CTA at most
+constexpr unsigned long long kTmaWaitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Waits for the phase with the given parity; gives up (timeout bit) after kTmaWaitNs.
+__device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned parity, LevelState* st) {
+  if (mbar_try_wait(bar, parity)) return;
+  const unsigned long long t0 = timer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (timer_ns() - t0 > kTmaWaitNs) {
+      atomicOr(&st->error, kErrTimeout);
+      return;
+    }
+  }
+}
+
+template <class Body, int CF>
+__device__ __forceinline__ void child_agg_staged(const BodyArgs& b, const int4* rec, const int* boff, int nrec,
+                                                 int total, int cb, bool count_blocks, int* s_stage, int* s_stage_n,
+                                                 int* s_stage_base) {
+  __shared__ __align__(16) int s_col[kTmaSubs][kTmaItems];
+  __shared__ __align__(16) unsigned s_w[kTmaSubs][kTmaItems];
+  __shared__ __align__(8) unsigned long long s_bar[kTmaSubs];
+  constexpr bool kW = Body::kStage == 2;
+  if (threadIdx.x == 0) *s_stage_n = 0;
+  const int per_cta = (int)blockDim.x / cb;
+  const int local = (int)threadIdx.x / cb, stid = (int)threadIdx.x % cb;
+  const int sub = (int)blockIdx.x * per_cta + local;
+  const int chunk = ceil_div(total, (int)gridDim.x * per_cta);
+  const int first = sub * chunk;
+  const int last = min(total, first + chunk);
+  const int span = cb * CF;
+  unsigned long long* bar = &s_bar[local];
+  if (stid == 0) mbar_init(bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  StageSink sink{b.next, b.next_count, s_stage, s_stage_n};
+  auto sub_sync = [&]() {
+    if (cb == 32)
+      __syncwarp();
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + local), "r"(cb) : "memory");
+  };
+  // stage items [bl * span, min(N, (bl + 1) * span)) of a parent whose list starts at `base`
+  auto stage = [&](int base, int N, int bl, int& a0, int& a1) -> bool {
+    const int e0 = base + bl * span, e1 = base + min(N, (bl + 1) * span);
+    a0 = (e0 + 3) & ~3;
+    a1 = e1 & ~3;
+    if (a1 <= a0) return false;
+    if (stid == 0) {
+      const unsigned bytes = (unsigned)(a1 - a0) * 4u;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(bar, kW ? 2u * bytes : bytes);
+      bulk_to_smem(&s_col[local][0], b.col + a0, bytes, bar);
+      if constexpr (kW) bulk_to_smem(&s_w[local][0], b.w + a0, bytes, bar);
+    }
+    return true;
+  };
+  int j = -1, off = 0, next_off = 0, next2 = 0x7fffffff, N = 0, base = 0;
+  int4 rn = make_int4(0, 0, 0, 0);
+  typename Body::P p{};
+  int ca0 = 0, ca1 = 0;
+  bool cur = false;
+  unsigned phase = 0;
+  if (first < last) {
+    j = warp_search(boff, 0, nrec, first);
+    const int4 r = __ldcg(&rec[j]);
+    off = __ldcg(&boff[j]);
+    next_off = j + 1 < nrec ? __ldcg(&boff[j + 1]) : 0x7fffffff;
+    N = r.z;
+    base = r.y;
+    p = Body::parent(b, r.x, r.y, r.z);
+    if (j + 1 < nrec) rn = __ldcg(&rec[j + 1]);
+    next2 = j + 2 < nrec ? __ldcg(&boff[j + 2]) : 0x7fffffff;
+    cur = stage(base, N, first - off, ca0, ca1);
+  }
+  for (int B0 = first; B0 < last; B0++) {
+    const int bl = B0 - off;
+    if (cur) {
+      mbar_wait(bar, phase, b.st);
+      phase ^= 1u;
+    }
+    typename Body::F f[CF];
+    bool v[CF];
+    int idx[CF];
+#pragma unroll
+    for (int k = 0; k < CF; k++) {
+      idx[k] = (bl * CF + k) * cb + stid;
+      v[k] = idx[k] < N;
+      const int e = base + idx[k];
+      if (!v[k])
+        f[k] = typename Body::F{};
+      else if (cur && e >= ca0 && e < ca1)
+        f[k] = Body::fetch_from(p, s_col[local][e - ca0], kW ? s_w[local][e - ca0] : 0u);
+      else
+        f[k] = Body::fetch(b, p, idx[k]);
+    }
+    sub_sync();   // the buffer is free again
+    // the next block: same parent, or (blocks are contiguous and a launching
+    // parent has at least one) parent j + 1; stage its lists now
+    bool nxt = false;
+    int na0 = 0, na1 = 0;
+    if (B0 + 1 < last) {
+      if (B0 + 1 < next_off)
+        nxt = stage(base, N, bl + 1, na0, na1);
+      else if (B0 + 1 < next2)
+        nxt = stage(rn.y, rn.z, 0, na0, na1);
+    }
+    bool pf[CF];
+    int pv[CF];
+    typename Body::P pk[CF];
+#pragma unroll
+    for (int k = 0; k < CF; k++) pk[k] = p;
+    Body::template apply_batch<CF>(b, pk, idx, f, v, pf, pv);
+    if constexpr (Body::kPushes) sink.template push<CF>(pf, pv);
+    if (B0 + 1 < last && B0 + 1 >= next_off) {
+      int4 r;
+      if (B0 + 1 < next2) {
+        j++;
+        r = rn;
+        off = next_off;
+        next_off = next2;
+      } else {
+        j = warp_search_near(boff, j + 1, nrec, B0 + 1);
+        r = __ldcg(&rec[j]);
+        off = __ldcg(&boff[j]);
+        next_off = j + 1 < nrec ? __ldcg(&boff[j + 1]) : 0x7fffffff;
+      }
+      N = r.z;
+      base = r.y;
+      p = Body::parent(b, r.x, r.y, r.z);
+      if (j + 1 < nrec) rn = __ldcg(&rec[j + 1]);
+      next2 = j + 2 < nrec ? __ldcg(&boff[j + 2]) : 0x7fffffff;
+    }
+    cur = nxt;
+    ca0 = na0;
+    ca1 = na1;
+  }
+  if constexpr (Body::kPushes) stage_flush(s_stage, s_stage_n, b.next, b.next_count, s_stage_base);
+  if (count_blocks && stid == 0 && last > first) add_stat(b.st, S_CBLOCKS, (unsigned long long)(last - first));
+  __syncthreads();
+  if (stid == 0) mbar_inval(bar);
+}
+
 // Aggregated child blocks [0, total) of the records rec[0, nrec) with block
 // offsets boff: disaggregation + coarsened body. A CTA hosts blockDim.x / cb
 // child blocks of cb threads that run independently (no CTA barrier on this
@@ -956,6 +1157,13 @@ __device__ __forceinline__ void child_agg_run(const BodyArgs& b, const int4* rec
   if constexpr (Body::kBalance) {
     if (ticket) {
       child_agg_balanced<Body, CF>(b, rec, boff, nrec, total, cb, ticket, s_stage_n);
+      return;
+    }
+  }
+  if constexpr (NP_TMA_STAGE && Body::kStage > 0 && CF <= 8) {
+    const bool aligned = (((unsigned long long)b.col | (Body::kStage == 2 ? (unsigned long long)b.w : 0ull)) & 15ull) == 0;
+    if (aligned && cb * CF <= kTmaItems && (int)blockDim.x / cb <= kTmaSubs) {
+      child_agg_staged<Body, CF>(b, rec, boff, nrec, total, cb, count_blocks, s_stage, s_stage_n, s_stage_base);
       return;
     }
   }
