@@ -589,7 +589,9 @@ def run_ours(args, ws, rank, local):
     elif wl["kind"] == "tc":
         per_solve = 4          # level-state reset, parent, child, partial-count sum
     else:
-        per_solve = 1 + st["graph_iterations"] * (2 * cfg.unroll + 1)
+        # init + while-body iterations x (unroll x (parent, child) + condition) (+ the SSSP
+        # distances written from the packed state)
+        per_solve = 1 + st["graph_iterations"] * (2 * cfg.unroll + 1) + (1 if wl["kind"] == "sssp" else 0)
     gpu_launches = int(per_solve * args.steps)
     metric = METRIC if args.workload == "sssp-rmat20" else \
         f"{W.unit} and ms/solve ({args.workload}): aggregated form vs plain CDP; % HBM roofline"
