@@ -1085,6 +1085,58 @@ def run_serving(args, ws, rank, local, wl):
     print(json.dumps(line), flush=True)
 
 
+def sweep_variants(npb):
+    """(name, config) of the variants the paper compares (Section VII): No CDP, plain CDP, T, C,
+    T+C, A at every granularity with and without T and C, and the threshold sweep of T+C+A."""
+    out = [("nodp", npb.config("nodp")), ("cdp", npb.config("cdp")), ("t", npb.config("t"))]
+    out += [(f"c{cf}", npb.config("c", cfactor=cf)) for cf in (2, 4, 8, 16)]
+    out += [("tc", npb.config("tc"))]
+    grans = [("warp", dict(granularity="warp")), ("block", dict(granularity="block"))]
+    grans += [(f"multiblock{gb}", dict(granularity="multiblock", group_blocks=gb)) for gb in (2, 4, 8, 16, 32)]
+    grans += [("grid_device", dict(granularity="grid_device")), ("grid_host", dict(granularity="grid_host"))]
+    for gname, kw in grans:
+        out.append((f"a_{gname}", npb.config("a", **kw)))
+        out.append((f"tca_{gname}", npb.config("tca", **kw)))
+    out += [(f"tca_grid_host_T{1 << k}", npb.config("tca", threshold=1 << k)) for k in range(17)]
+    out += [(f"tca_grid_host_C{cf}", npb.config("tca", cfactor=cf)) for cf in (1, 2, 8, 16)]
+    return out
+
+
+def run_sweep(args, local, wl):
+    """Every variant of the comparison on one workload: median ms/solve over a few solves,
+    the device-side counters, and equality with the headline form's result."""
+    import torch
+    from paper_2201_02789_gb300 import build as nbuild
+    from paper_2201_02789_gb300 import nestpar as npb
+    nbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = npb.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.int8, device=dev)
+    if wl["kind"] == "bezier":
+        W = BezierWorkload(dev, stream, ctx)
+    elif wl["kind"] == "tc":
+        W = TcWorkload(dev, stream, ctx)
+    else:
+        W = GraphWorkload(wl["kind"], load_graph(wl["graph"]), dev, stream, ctx)
+    head = npb.config("tca", **TUNED.get(args.workload, {}))
+    W.solve(head)
+    ref = W.result()
+    units = W.units()
+    for name, cfg in sweep_variants(npb):
+        W.solve(cfg)
+        reps = 2 if name in ("cdp", "t") or name.startswith("c") and not name.startswith("c_") else 5
+        ms = statistics.median(time_solves(lambda: W.solve(cfg), reps, flush, stream))
+        _, st = W.solve(cfg, stats=True)
+        print(json.dumps({"workload": args.workload, "variant": name, "config": cfg.as_dict(), "ms_per_solve": ms,
+                          "value": units / (ms * 1e-3) / 1e9, "unit": W.unit,
+                          "device_launches": st["device_launches"], "launch_failures": st["launch_failures"],
+                          "child_items": st["child_items"], "items": st["items"],
+                          "matches_headline": bool(np.array_equal(W.result(), ref))}), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -1096,6 +1148,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time every variant of the paper's comparison on the workload (one JSON line each)")
     ap.add_argument("--only-headline", action="store_true",
                     help="headline form and three profile-mode solves only (for profiler captures)")
     args = ap.parse_args()
@@ -1106,6 +1160,9 @@ def main():
         run_reference(args, ws, rank)
         return
     wl = WORKLOADS[args.workload]
+    if args.sweep:
+        run_sweep(args, local, wl)
+        return
     if wl["kind"] == "batched":
         run_batched(args, ws, rank, local, wl)
     elif wl["kind"] == "serving":

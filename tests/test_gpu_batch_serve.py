@@ -297,3 +297,46 @@ def test_server_rejects_device_launch_forms(ctx, serve_graphs):
     _, devs = serve_graphs
     s = npb.np_server_create(ctx.handle, [devs[0].csr], bfs_cfg=npb.config("cdp"), check=False)
     assert s == npb.NP_ERR_UNSUPPORTED
+
+
+@pytest.mark.slow
+def test_server_full_size_sampled(ctx):
+    """The serving workload's graphs (R-MAT scales 16..22, edge factor 16): a mix of BFS and
+    SSSP queries submitted in waves while others are resident; a sample checked against the
+    oracle (queries on the largest graphs included) and against single solves."""
+    from concurrent.futures import ThreadPoolExecutor
+    graphs = [gen.rmat(s, 16, seed=5 * 1000 + s) for s in range(16, 23)]
+    devs = [DevGraph(g) for g in graphs]
+    sv = npb.np_server_create(ctx.handle, [d.csr for d in devs], max_slots=16, levels_per_step=2,
+                              bfs_cfg=npb.config("tca"), sssp_cfg=npb.config("tca"))
+    try:
+        qs = []
+        for gi, g in enumerate(graphs):
+            for kind in (0, 1):
+                for s in gen.random_sources(g, 3, seed=500 + 2 * gi + kind):
+                    qs.append((gi, kind, int(s)))
+        outs, ticks, pending = {}, {}, list(range(len(qs)))
+        for step in range(100000):
+            for _ in range(4):
+                if pending:
+                    q = pending.pop(0)
+                    gi, kind, s = qs[q]
+                    outs[q] = torch.empty((graphs[gi].n,), dtype=torch.int32, device=DEV)
+                    ticks[q] = npb.np_server_submit(sv, gi, kind, s, outs[q])
+            if npb.np_server_step(sv) == 0 and not pending:
+                break
+        assert all(npb.np_server_poll(sv, t)["done"] for t in ticks.values())
+        sample = [q for q in range(len(qs)) if q % 3 == 0]
+        with ThreadPoolExecutor(8) as ex:
+            refs = list(ex.map(lambda q: _ref(graphs[qs[q][0]], qs[q][1], qs[q][2]), sample))
+        for q, ref in zip(sample, refs):
+            gi, kind, s = qs[q]
+            got = outs[q].cpu().numpy()
+            np.testing.assert_array_equal(got.view(np.uint32) if kind else got, ref, err_msg=f"query {q}")
+        for q in range(0, len(qs), 7):
+            gi, kind, s = qs[q]
+            alone = torch.empty((graphs[gi].n,), dtype=torch.int32, device=DEV)
+            (npb.np_sssp if kind else npb.np_bfs)(ctx.handle, devs[gi].csr, s, alone, npb.config("tca"))
+            assert torch.equal(alone, outs[q]), q
+    finally:
+        npb.np_server_destroy(sv)
