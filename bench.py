@@ -1099,6 +1099,11 @@ def sweep_variants(npb):
         out.append((f"tca_{gname}", npb.config("tca", **kw)))
     out += [(f"tca_grid_host_T{1 << k}", npb.config("tca", threshold=1 << k)) for k in range(17)]
     out += [(f"tca_grid_host_C{cf}", npb.config("tca", cfactor=cf)) for cf in (1, 2, 8, 16)]
+    # the dead-launch-code pair (Section VII-D): the same CTA-tiled parent kernel without and
+    # with a launch site that never runs, driven the same way
+    chunk = dict(driver=npb.NP_DRIVER_CHUNK)
+    out += [("nodp_cta_no_launch_code", npb.config("nodp", granularity="none", **chunk)),
+            ("cdp_threshold_above_max_degree", npb.config("cdp", threshold=npb.INT32_MAX, **chunk))]
     return out
 
 
@@ -1124,7 +1129,10 @@ def run_sweep(args, local, wl):
     W.solve(head)
     ref = W.result()
     units = W.units()
+    only = set(args.variants.split(",")) if args.variants else None
     for name, cfg in sweep_variants(npb):
+        if only is not None and name not in only:
+            continue
         W.solve(cfg)
         reps = 2 if name in ("cdp", "t") or name.startswith("c") and not name.startswith("c_") else 5
         ms = statistics.median(time_solves(lambda: W.solve(cfg), reps, flush, stream))
@@ -1150,6 +1158,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sweep", action="store_true",
                     help="time every variant of the paper's comparison on the workload (one JSON line each)")
+    ap.add_argument("--variants", default="", help="with --sweep: comma-separated variant names to run")
     ap.add_argument("--only-headline", action="store_true",
                     help="headline form and three profile-mode solves only (for profiler captures)")
     args = ap.parse_args()
