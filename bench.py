@@ -84,7 +84,10 @@ WORKLOADS = {
 
 # per-workload values of the aggregated form's knobs, from threshold x cfactor x child-block
 # sweeps on GB300 (the paper also tunes T and CF per benchmark); other workloads use the defaults
-TUNED = {"bt64k": dict(child_block=32, cfactor=8), "tc-rmat17": dict(threshold=8)}
+TUNED = {"bt64k": dict(child_block=32, cfactor=8), "tc-rmat17": dict(threshold=8),
+         # the 4096-vertex graph is latency-bound: the persistent level loop on 8 CTAs keeps its
+         # per-level grid barriers cheap (124 us against 141 us with the graph driver)
+         "bfs4k": dict(driver=4, parent_grid=8)}   # driver 4: NP_DRIVER_PERSISTENT
 
 
 def log(*a):
@@ -591,7 +594,8 @@ def run_ours(args, ws, rank, local):
     else:
         # init + while-body iterations x (unroll x (parent, child) + condition) (+ the SSSP
         # distances written from the packed state)
-        per_solve = 1 + st["graph_iterations"] * (2 * cfg.unroll + 1) + (1 if wl["kind"] == "sssp" else 0)
+        loop = 1 if cfg.driver == npb.NP_DRIVER_PERSISTENT else st["graph_iterations"] * (2 * cfg.unroll + 1)
+        per_solve = 1 + loop + (1 if wl["kind"] == "sssp" else 0)
     gpu_launches = int(per_solve * args.steps)
     metric = METRIC if args.workload == "sssp-rmat20" else \
         f"{W.unit} and ms/solve ({args.workload}): aggregated form vs plain CDP; % HBM roofline"
@@ -678,7 +682,9 @@ def run_ours(args, ws, rank, local):
             "vs_baseline": None, "dtype": {"bezier": "f32", "tc": "i32"}.get(wl["kind"], "u32"), "data": "synthetic",
             "config": dict(wl["config"], l2=L2_NOTE),
             "form": f"threshold {cfg.threshold} + coarsening {cfg.cfactor} ({cfg.child_block}-thread child blocks) "
-                    "+ grid aggregation (atomic scan), while-graph level loop",
+                    "+ grid aggregation (atomic scan), " + (
+                        f"persistent cooperative level loop on {cfg.parent_grid} CTAs"
+                        if cfg.driver == npb.NP_DRIVER_PERSISTENT else "while-graph level loop"),
             "ms_per_solve": {"median": statistics.median(ms), "min": min(ms)},
             "units_per_solve": units, "levels": st["levels"], "child_items": st["items"],
             "speedup_vs_plain_cdp": forms["plain_cdp"]["ms_per_solve"] / statistics.median(ms),

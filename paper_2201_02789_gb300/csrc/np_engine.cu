@@ -680,7 +680,10 @@ np_status launch_level_loop(Engine& e, const Plan& p, const Args& a, const np_co
   if (blk < cb) blk = cb;
   blk = (blk + cb - 1) / cb * cb;
   if (blk > 1024) return NP_ERR_UNSUPPORTED;
-  const int grid = occupancy(e, p.loop, blk) * e.sms;
+  // the whole resident grid, or parent_grid CTAs (a small grid keeps the
+  // per-level barriers cheap on small problems)
+  const int full = occupancy(e, p.loop, blk) * e.sms;
+  const int grid = cfg.parent_grid > 0 && cfg.parent_grid < full ? cfg.parent_grid : full;
   Args aa = a;
   aa.k = 0;
   int ml = max_levels;
