@@ -87,6 +87,9 @@ EXTRA = [
     ("persistent-pb384-cb256", dict(driver=npb.NP_DRIVER_PERSISTENT, parent_block=384, child_block=256,
                                     threshold=2)),
     ("persistent-nodp", dict(variant=npb.NP_VARIANT_NODP, driver=npb.NP_DRIVER_PERSISTENT)),
+    ("persistent-grid1", dict(driver=npb.NP_DRIVER_PERSISTENT, parent_grid=1)),
+    ("persistent-grid3-T1", dict(driver=npb.NP_DRIVER_PERSISTENT, parent_grid=3, threshold=1)),
+    ("persistent-grid8-nodp", dict(variant=npb.NP_VARIANT_NODP, driver=npb.NP_DRIVER_PERSISTENT, parent_grid=8)),
 ]
 
 
