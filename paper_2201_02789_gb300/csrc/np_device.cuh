@@ -70,6 +70,18 @@
 #ifndef NP_SPREAD_BATCH
 #define NP_SPREAD_BATCH 8
 #endif
+// The load that filters a child item before its atomic (level[v] for BFS,
+// dist(v) for SSSP). Only the atomic decides, and a stale value can only be
+// an older one (levels are claimed once, distances only fall), so a filter
+// read through L1 (1) can cost an unneeded atomic but never a wrong result.
+#ifndef NP_FILTER_L1
+#define NP_FILTER_L1 1
+#endif
+#if NP_FILTER_L1
+#define NP_FILTER_LOAD(p) __ldca(p)
+#else
+#define NP_FILTER_LOAD(p) __ldcg(p)
+#endif
 // 1: a relaxation reads dist(v) first and issues the atomic only when it would
 // lower it; 0: every relaxation issues the atomic (one dependent round trip
 // fewer, more atomics)
@@ -547,7 +559,7 @@ struct BfsBody {
 #pragma unroll
     for (int k = 0; k < K; k++) {
       v[k] = f[k].v;
-      cur[k] = valid[k] ? __ldcg(&b.level[v[k]]) : 0;
+      cur[k] = valid[k] ? NP_FILTER_LOAD(&b.level[v[k]]) : 0;
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -733,7 +745,7 @@ struct Sssp64Body {
       const unsigned long long s = (unsigned long long)p[k].du + f[k].w;
       nd[k] = ((s >= 0xffffffffull ? 0xfffffffeull : s) << 32) | tag;
 #if NP_SSSP_PRECHECK
-      cur[k] = (valid[k] && live[k]) ? __ldcg(&b.dtag[v[k]]) : 0ull;
+      cur[k] = (valid[k] && live[k]) ? NP_FILTER_LOAD(&b.dtag[v[k]]) : 0ull;
 #else
       cur[k] = 0xffffffffffffffffull;
 #endif
