@@ -613,7 +613,7 @@ struct SsspBody {
       live[k] = p[k].du != 0xffffffffu;
       const unsigned long long s = (unsigned long long)p[k].du + f[k].w;
       nd[k] = s >= 0xffffffffull ? 0xfffffffeu : (unsigned)s;
-      cur[k] = (valid[k] && live[k]) ? __ldcg(&b.dist[v[k]]) : 0u;
+      cur[k] = (valid[k] && live[k]) ? NP_FILTER_LOAD(&b.dist[v[k]]) : 0u;
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {
