@@ -1524,10 +1524,21 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
   StageSink sink{b.next, b.next_count, s_stage, s_stage_n};
   unsigned long long n_par = 0, n_items = 0, n_serial = 0, n_launch = 0, n_citems = 0;
 
+  // Without look-back waits (atomic aggregation scan, no output offsets) no
+  // tile waits on another, so each warp's first tile is its own index and
+  // only later tiles come from the ticket: small levels skip that round trip.
+  // With look-back, tiles are taken strictly in ticket order (a wait only ever
+  // targets a tile that a running warp holds).
+  const bool static_first = a.scan != 0 && !Body::kOffsets;
+  const int warps_total = (int)gridDim.x * ((int)blockDim.x >> 5);
+  int own_tile = static_first ? (int)blockIdx.x * ((int)blockDim.x >> 5) + ((int)threadIdx.x >> 5) : -1;
   for (;;) {
-    int tile = 0;
-    if (lane == 0) tile = atomicAdd(&st->ticket[slot], 1);
-    tile = __shfl_sync(kFull, tile, 0);
+    int tile = own_tile;
+    if (tile < 0) {
+      if (lane == 0) tile = atomicAdd(&st->ticket[slot], 1) + (static_first ? warps_total : 0);
+      tile = __shfl_sync(kFull, tile, 0);
+    }
+    own_tile = -1;   // later tiles come from the ticket
     if (tile >= ntiles) break;
     const int i = tile * 32 + lane;
     int pid = 0, base = 0, N = 0;
