@@ -422,6 +422,7 @@ struct WarpSink {
     int c = 0;
 #pragma unroll
     for (int k = 0; k < K; k++) c += pf[k] ? 1 : 0;
+    if (!__any_sync(kFull, c != 0)) return;   // most batches append nothing: skip the scan
     const int lane = threadIdx.x & 31;
     int inc = c;
 #pragma unroll
@@ -453,6 +454,7 @@ struct StageSink {
     int c = 0;
 #pragma unroll
     for (int k = 0; k < K; k++) c += pf[k] ? 1 : 0;
+    if (!__any_sync(kFull, c != 0)) return;   // most batches append nothing: skip the scan
     const int lane = threadIdx.x & 31;
     int inc = c;
 #pragma unroll

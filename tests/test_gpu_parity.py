@@ -390,6 +390,28 @@ def test_bt64k_full(ctx):
     assert ok, worst
 
 
+def test_bench_tuned_configs_full(ctx, g4k):
+    """The configurations bench.py times where they differ from the library default (BT-64K
+    with 32-thread child blocks and CF 8; the 4096-vertex BFS on the persistent loop with 8
+    CTAs), at full size, against the oracle."""
+    import bench
+    cfg = npb.config("tca", **bench.TUNED["bt64k"])
+    ctrl = gen.bt64k()
+    ref_off, ref_pts = oracle.bezier(ctrl)
+    status, off, pts, st = bezier(ctx, ctrl, cfg, cap=int(ref_off[-1]))
+    assert status == npb.NP_OK and st["error"] == 0
+    np.testing.assert_array_equal(off, ref_off)
+    ok, worst = bezier_tolerance_ok(pts, ref_pts)
+    assert ok, worst
+    g, dg, ref_l, ref_d = g4k
+    cfg = npb.config("tca", **bench.TUNED["bfs4k"])
+    lv, st = bfs(ctx, dg, 0, cfg, stats=True)
+    np.testing.assert_array_equal(lv, ref_l)
+    d, st2 = sssp(ctx, dg, 0, cfg, stats=True)
+    np.testing.assert_array_equal(d, ref_d)
+    assert st["error"] == 0 and st2["error"] == 0
+
+
 # ------------------------------------------------------------------ stress
 
 @pytest.mark.parametrize("scan", [npb.NP_SCAN_LOOKBACK, npb.NP_SCAN_ATOMIC], ids=["lookback", "atomic"])

@@ -198,8 +198,10 @@ def test_gpu_triangles_full_size(ctx):
     """The benchmark's workload: R-MAT scale 17 made simple and undirected (3.7e6 edges,
     36,004,405 triangles)."""
     from paper_2201_02789_gb300 import nestpar as npb
+    import bench
     u, dag = gen.tc_rmat17()
     ref = oracle.triangles(u.row_ptr, u.col)
-    for cfg in (npb.config("tca"), npb.config("nodp")):
+    # the library default, the configuration bench.py times, and the No-CDP form
+    for cfg in (npb.config("tca"), npb.config("tca", **bench.TUNED["tc-rmat17"]), npb.config("nodp")):
         got, st = _gpu_count(ctx, dag, cfg)
         assert got == ref and st["error"] == 0
