@@ -398,6 +398,45 @@ class GraphWorkload:
         h2d = 4 * (g.n + 1) + (8 if self.kind == "sssp" else 4) * g.m
         return ms, h2d, 4 * g.n, res
 
+    def e2e_pipelined(self, cfg, steps, flush, dev):
+        """The stream-ordered host calls (np_*_host_async) alternating over two contexts on two
+        streams, so that one step's copies run while the other context solves. Every step
+        still copies its whole graph in from pinned memory and its result out; the L2 flush
+        runs on the step's own stream before its copies. Returns ms per step over the run."""
+        import torch
+        g = self.g
+        ctxs = [self.ctx, self.npb.Context(dev.index)]
+        streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+        rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+        col_h = torch.from_numpy(g.col).pin_memory()
+        w_h = torch.from_numpy(g.w.view(np.int32)).pin_memory() if self.kind == "sssp" else None
+        outs = [torch.empty(g.n, dtype=torch.int32).pin_memory() for _ in range(2)]
+
+        def step(k):
+            c, s = ctxs[k % 2], streams[k % 2]
+            with torch.cuda.stream(s):
+                flush.zero_()
+            if self.kind == "sssp":
+                self.npb.np_sssp_host_async(c.handle, rp_h, col_h, w_h, 0, outs[k % 2], cfg, stream=s)
+            else:
+                self.npb.np_bfs_host_async(c.handle, rp_h, col_h, 0, outs[k % 2], cfg, stream=s)
+
+        try:
+            for k in range(4):   # warm-up: both contexts build their graphs and staging buffers
+                step(k)
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            for k in range(steps):
+                step(k)
+            torch.cuda.synchronize(dev)
+            ms = (time.perf_counter() - t) * 1e3 / steps
+            for c, s in zip(ctxs, streams):
+                self.npb.np_sync(c.handle, stream=s)
+            res = [o.numpy().view(np.uint32) if self.kind == "sssp" else o.numpy().copy() for o in outs]
+        finally:
+            ctxs[1].close()
+        return ms, res
+
 
 class BezierWorkload:
     """Tessellation of the 64K-curve set through np_bezier."""
@@ -667,7 +706,18 @@ def run_ours(args, ws, rank, local):
     e2e = {"value": units / (statistics.median(e2e_ms) * 1e-3) / 1e9, "unit": W.unit,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
            "ms_per_step": statistics.median(e2e_ms),
-           "matches_device_result": bool(np.array_equal(e2e_res, res_gpu))}
+           "matches_device_result": bool(np.array_equal(e2e_res, res_gpu)),
+           "mode": "one waiting call per step (np_*_host), median step"}
+    if hasattr(W, "e2e_pipelined"):
+        # the headline end-to-end figure: steps overlap on two contexts; the waiting form
+        # stays beside it
+        p_ms, p_res = W.e2e_pipelined(cfg, max(args.e2e_steps, 8), flush, dev)
+        e2e = {"value": units / (p_ms * 1e-3) / 1e9, "unit": W.unit,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": p_ms,
+               "matches_device_result": bool(all(np.array_equal(r, res_gpu) for r in p_res)) and
+               e2e["matches_device_result"],
+               "mode": "stream-ordered calls (np_*_host_async) alternating over 2 contexts and 2 streams",
+               "waiting_call": {k: e2e[k] for k in ("value", "ms_per_step")}}
 
     # CPU baseline: the oracle as it stands, one core, bounded sample; also the parity check
     cpu = None

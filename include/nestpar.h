@@ -409,6 +409,23 @@ np_status np_sssp_host(np_ctx *ctx, int32_t n, int64_t m, const int32_t *row_ptr
                        const int32_t *col_idx_host, const uint32_t *weights_host, int32_t src,
                        uint32_t *dist_host, const np_config *cfg, void *stream, np_stats *stats);
 
+/* Stream-ordered forms of np_bfs_host / np_sssp_host: they enqueue the copies in,
+ * the solve and the copy out on `stream` and return without waiting. The host
+ * buffers must stay valid, and the inputs unchanged, until the stream has passed
+ * the call; the result is in `level_host` / `dist_host` from then on. Only
+ * page-locked host buffers (cudaHostAlloc, cudaHostRegister) let the copies run
+ * asynchronously; with pageable memory the runtime copies synchronously. The
+ * staging buffers belong to the context, so calls on one context must be
+ * ordered on one stream; two contexts on two streams let one call's copies
+ * overlap the other's solve. Argument errors return synchronously, as for the
+ * waiting forms; device errors are reported by the next np_sync on the context. */
+np_status np_bfs_host_async(np_ctx *ctx, int32_t n, int64_t m, const int32_t *row_ptr_host,
+                            const int32_t *col_idx_host, int32_t src, int32_t *level_host,
+                            const np_config *cfg, void *stream);
+np_status np_sssp_host_async(np_ctx *ctx, int32_t n, int64_t m, const int32_t *row_ptr_host,
+                             const int32_t *col_idx_host, const uint32_t *weights_host, int32_t src,
+                             uint32_t *dist_host, const np_config *cfg, void *stream);
+
 /* ---- execution-time breakdown (the paper's Section VII-B, measured instead of
  *      obtained by deactivating code) ---- */
 #define NP_PROFILE_LEVELS 64

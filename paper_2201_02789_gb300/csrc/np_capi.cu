@@ -45,7 +45,7 @@ np_status ensure_dtag(np_ctx* c, int64_t total) {
   return NP_OK;
 }
 
-constexpr int kVersion = 10100;  // 1.1.0
+constexpr int kVersion = 10200;  // 1.2.0
 
 // One graph solve (kind 0 BFS, 1 SSSP) on device arrays.
 np_status solve(np_ctx* c, int kind, const np_csr* g, int src, int* level, unsigned* dist,
@@ -223,6 +223,44 @@ np_status stage_bytes(np_ctx* c, size_t bytes) {
   NP_CK(cudaMalloc(&c->stage, bytes));
   c->stage_bytes = bytes;
   return NP_OK;
+}
+
+// BFS (kind 0) or SSSP (kind 1) of a CSR graph in host memory: copies the graph
+// into the context's staging buffer, solves, copies the result out, all on
+// `stream`; with `wait`, then waits and reads the device status.
+np_status host_solve(np_ctx* c, int kind, int32_t n, int64_t m, const int32_t* row_ptr_host,
+                     const int32_t* col_idx_host, const uint32_t* weights_host, int32_t src, void* out_host,
+                     const np_config* cfg, void* stream, np_stats* stats, bool wait) {
+  if (!c || n < 1 || m < 0 || m >= INT_MAX || !row_ptr_host || (m > 0 && !col_idx_host) ||
+      (kind == 1 && m > 0 && !weights_host) || !out_host)
+    return NP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t b_rp = align_up(sizeof(int32_t) * ((size_t)n + 1)), b_col = align_up(sizeof(int32_t) * (size_t)m);
+  const size_t b_w = kind == 1 ? b_col : 0, b_out = align_up(sizeof(int32_t) * (size_t)n);
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    NP_CK(cudaSetDevice(c->e.device));
+    np_status st = stage_bytes(c, b_rp + b_col + b_w + b_out);
+    if (st != NP_OK) return st;
+  }
+  int32_t* d_rp = reinterpret_cast<int32_t*>(c->stage);
+  int32_t* d_col = reinterpret_cast<int32_t*>(c->stage + b_rp);
+  uint32_t* d_w = kind == 1 ? reinterpret_cast<uint32_t*>(c->stage + b_rp + b_col) : nullptr;
+  int32_t* d_out = reinterpret_cast<int32_t*>(c->stage + b_rp + b_col + b_w);
+  NP_CK(cudaMemcpyAsync(d_rp, row_ptr_host, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s));
+  if (m) {
+    NP_CK(cudaMemcpyAsync(d_col, col_idx_host, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+    if (kind == 1) NP_CK(cudaMemcpyAsync(d_w, weights_host, sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+  }
+  np_csr g{d_rp, d_col, d_w, n, m};
+  np_status st = kind == 1 ? np_sssp(c, &g, src, reinterpret_cast<uint32_t*>(d_out), cfg, stream, nullptr)
+                           : np_bfs(c, &g, src, d_out, cfg, stream, nullptr);
+  if (st != NP_OK) return st;
+  NP_CK(cudaMemcpyAsync(out_host, d_out, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+  if (!wait) return NP_OK;
+  NP_CK(cudaStreamSynchronize(s));
+  np_stats tmp;
+  return np_sync(c, stream, stats ? stats : &tmp);
 }
 
 }  // namespace
@@ -453,62 +491,26 @@ np_status np_run_nested(np_ctx* c, const np_parents* parents, int32_t count_kind
 
 np_status np_bfs_host(np_ctx* c, int32_t n, int64_t m, const int32_t* row_ptr_host, const int32_t* col_idx_host,
                       int32_t src, int32_t* level_host, const np_config* cfg, void* stream, np_stats* stats) {
-  if (!c || n < 1 || m < 0 || m >= INT_MAX || !row_ptr_host || (m > 0 && !col_idx_host) || !level_host)
-    return NP_ERR_INVALID;
-  cudaStream_t s = (cudaStream_t)stream;
-  size_t b_rp = align_up(sizeof(int32_t) * ((size_t)n + 1)), b_col = align_up(sizeof(int32_t) * (size_t)m);
-  size_t b_out = align_up(sizeof(int32_t) * (size_t)n);
-  {
-    std::lock_guard<std::mutex> lk(c->mu);
-    NP_CK(cudaSetDevice(c->e.device));
-    np_status st = stage_bytes(c, b_rp + b_col + b_out);
-    if (st != NP_OK) return st;
-  }
-  int32_t* d_rp = reinterpret_cast<int32_t*>(c->stage);
-  int32_t* d_col = reinterpret_cast<int32_t*>(c->stage + b_rp);
-  int32_t* d_out = reinterpret_cast<int32_t*>(c->stage + b_rp + b_col);
-  NP_CK(cudaMemcpyAsync(d_rp, row_ptr_host, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s));
-  if (m) NP_CK(cudaMemcpyAsync(d_col, col_idx_host, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
-  np_csr g{d_rp, d_col, nullptr, n, m};
-  np_status st = np_bfs(c, &g, src, d_out, cfg, stream, nullptr);
-  if (st != NP_OK) return st;
-  NP_CK(cudaMemcpyAsync(level_host, d_out, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
-  NP_CK(cudaStreamSynchronize(s));
-  np_stats tmp;
-  return np_sync(c, stream, stats ? stats : &tmp);
+  return host_solve(c, 0, n, m, row_ptr_host, col_idx_host, nullptr, src, level_host, cfg, stream, stats, true);
 }
 
 np_status np_sssp_host(np_ctx* c, int32_t n, int64_t m, const int32_t* row_ptr_host, const int32_t* col_idx_host,
                        const uint32_t* weights_host, int32_t src, uint32_t* dist_host, const np_config* cfg,
                        void* stream, np_stats* stats) {
-  if (!c || n < 1 || m < 0 || m >= INT_MAX || !row_ptr_host || (m > 0 && (!col_idx_host || !weights_host)) ||
-      !dist_host)
-    return NP_ERR_INVALID;
-  cudaStream_t s = (cudaStream_t)stream;
-  size_t b_rp = align_up(sizeof(int32_t) * ((size_t)n + 1)), b_col = align_up(sizeof(int32_t) * (size_t)m);
-  size_t b_out = align_up(sizeof(uint32_t) * (size_t)n);
-  {
-    std::lock_guard<std::mutex> lk(c->mu);
-    NP_CK(cudaSetDevice(c->e.device));
-    np_status st = stage_bytes(c, b_rp + 2 * b_col + b_out);
-    if (st != NP_OK) return st;
-  }
-  int32_t* d_rp = reinterpret_cast<int32_t*>(c->stage);
-  int32_t* d_col = reinterpret_cast<int32_t*>(c->stage + b_rp);
-  uint32_t* d_w = reinterpret_cast<uint32_t*>(c->stage + b_rp + b_col);
-  uint32_t* d_out = reinterpret_cast<uint32_t*>(c->stage + b_rp + 2 * b_col);
-  NP_CK(cudaMemcpyAsync(d_rp, row_ptr_host, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s));
-  if (m) {
-    NP_CK(cudaMemcpyAsync(d_col, col_idx_host, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
-    NP_CK(cudaMemcpyAsync(d_w, weights_host, sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
-  }
-  np_csr g{d_rp, d_col, d_w, n, m};
-  np_status st = np_sssp(c, &g, src, d_out, cfg, stream, nullptr);
-  if (st != NP_OK) return st;
-  NP_CK(cudaMemcpyAsync(dist_host, d_out, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
-  NP_CK(cudaStreamSynchronize(s));
-  np_stats tmp;
-  return np_sync(c, stream, stats ? stats : &tmp);
+  return host_solve(c, 1, n, m, row_ptr_host, col_idx_host, weights_host, src, dist_host, cfg, stream, stats, true);
+}
+
+np_status np_bfs_host_async(np_ctx* c, int32_t n, int64_t m, const int32_t* row_ptr_host,
+                            const int32_t* col_idx_host, int32_t src, int32_t* level_host, const np_config* cfg,
+                            void* stream) {
+  return host_solve(c, 0, n, m, row_ptr_host, col_idx_host, nullptr, src, level_host, cfg, stream, nullptr, false);
+}
+
+np_status np_sssp_host_async(np_ctx* c, int32_t n, int64_t m, const int32_t* row_ptr_host,
+                             const int32_t* col_idx_host, const uint32_t* weights_host, int32_t src,
+                             uint32_t* dist_host, const np_config* cfg, void* stream) {
+  return host_solve(c, 1, n, m, row_ptr_host, col_idx_host, weights_host, src, dist_host, cfg, stream, nullptr,
+                    false);
 }
 
 np_status np_selftest_wait(np_ctx* c, int32_t which, int64_t limit_ns, void* stream) {

@@ -160,6 +160,8 @@ _SIGS = {
                     ctypes.POINTER(np_stats)],
     "np_sssp_host": [_VP, _I32, _I64, _VP, _VP, _VP, _I32, _VP, ctypes.POINTER(np_config), _VP,
                      ctypes.POINTER(np_stats)],
+    "np_bfs_host_async": [_VP, _I32, _I64, _VP, _VP, _I32, _VP, ctypes.POINTER(np_config), _VP],
+    "np_sssp_host_async": [_VP, _I32, _I64, _VP, _VP, _VP, _I32, _VP, ctypes.POINTER(np_config), _VP],
     "np_bezier_noalloc": [_VP, _I32, _VP, _VP, _I64, ctypes.POINTER(np_config), _VP],
     "np_bezier_host": [_VP, _VP, _I32, _VP, _VP, _I64, ctypes.POINTER(np_config), _VP, ctypes.POINTER(np_stats)],
     "np_profile_enable": [_VP, _I32],
@@ -367,6 +369,23 @@ def np_sssp_host(ctx, row_ptr, col_idx, weights, src: int, dist_out, cfg=None, s
                            ctypes.byref(st) if want else None)
     _check(s, "np_sssp_host", check)
     return (s, st.as_dict()) if want else s
+
+
+def np_bfs_host_async(ctx, row_ptr, col_idx, src: int, level_out, cfg=None, stream=None, check: bool = True):
+    """Stream-ordered np_bfs_host: returns once the copies, the solve and the copy out are
+    enqueued on `stream`; the host arrays must stay alive until the stream passes the call."""
+    s = lib().np_bfs_host_async(ctx, int(row_ptr.shape[0] - 1), int(col_idx.shape[0]), _ptr(row_ptr),
+                                _ptr(col_idx), int(src), _ptr(level_out), ctypes.byref(_cfg(cfg)), _stream(stream))
+    return _check(s, "np_bfs_host_async", check)
+
+
+def np_sssp_host_async(ctx, row_ptr, col_idx, weights, src: int, dist_out, cfg=None, stream=None,
+                       check: bool = True):
+    """Stream-ordered np_sssp_host (see np_bfs_host_async)."""
+    s = lib().np_sssp_host_async(ctx, int(row_ptr.shape[0] - 1), int(col_idx.shape[0]), _ptr(row_ptr),
+                                 _ptr(col_idx), _ptr(weights), int(src), _ptr(dist_out), ctypes.byref(_cfg(cfg)),
+                                 _stream(stream))
+    return _check(s, "np_sssp_host_async", check)
 
 
 def np_profile_enable(ctx, on: bool = True) -> int:

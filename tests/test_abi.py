@@ -86,7 +86,7 @@ int main(void) {
 
 
 def test_host_only_entry_points(lib):
-    assert npb.np_version() == 10100
+    assert npb.np_version() == 10200
     assert npb.np_status_string(npb.NP_ERR_INVALID) == "invalid argument"
     cfg = npb.np_config_default()
     assert (cfg.variant, cfg.threshold, cfg.cfactor, cfg.granularity, cfg.scan) == (1, 32, 4, npb.NP_GRAN_GRID_HOST, npb.NP_SCAN_ATOMIC)
@@ -110,6 +110,8 @@ def test_host_argument_errors_of_new_entry_points(lib):
     assert L.np_batch_create(None, 0, None, None, None, None) == npb.NP_ERR_INVALID
     assert L.np_server_create(None, None, 0, None, None) == npb.NP_ERR_INVALID
     assert L.np_bfs_multi(None, None, 0, None, None, 0, None, None, None) == npb.NP_ERR_INVALID
+    assert L.np_bfs_host_async(None, 0, 0, None, None, 0, None, None, None) == npb.NP_ERR_INVALID
+    assert L.np_sssp_host_async(None, 1, 0, None, None, None, 0, None, None, None) == npb.NP_ERR_INVALID
     assert npb.multi_stride(1) == 1 and npb.multi_stride(4096) == 4096 and npb.multi_stride(4097) == 8192
 
 

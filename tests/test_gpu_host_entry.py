@@ -55,6 +55,41 @@ def test_graph_host_entry_edge_cases(ctx):
         npb.NP_ERR_INVALID
 
 
+def test_async_host_entry_points_on_two_contexts(ctx):
+    """The stream-ordered host calls on two contexts and two streams, issued back to back so
+    that one context's copies can overlap the other's solve, over graphs of different sizes
+    (the staging buffers grow between calls): every result equals the oracle's and np_sync
+    reports no device error."""
+    ctx2 = npb.Context(0)
+    try:
+        ctxs, streams = [ctx, ctx2], [torch.cuda.Stream(), torch.cuda.Stream()]
+        graphs = [(gen.rmat(14, 8, seed=93), 3), (gen.bfs4k(), 0), (gen.road_grid(30, 20, seed=7), 11),
+                  (gen.rmat(12, 16, seed=94), 0), (gen.rmat(15, 4, seed=95), 5)]
+        bufs = []
+        for g, _ in graphs:
+            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            bufs.append((pin(g.row_ptr), pin(g.col), pin(g.w.view(np.int32)),
+                         torch.full((g.n,), 9, dtype=torch.int32).pin_memory(),
+                         torch.full((g.n,), 9, dtype=torch.int32).pin_memory()))
+        cfg = npb.config("tca")
+        for rep in range(2):
+            for k, ((g, src), (rp, col, w, lv, d)) in enumerate(zip(graphs, bufs)):
+                c, s = ctxs[(k + rep) % 2], streams[(k + rep) % 2]
+                npb.np_bfs_host_async(c.handle, rp, col, src, lv, cfg, stream=s)
+                npb.np_sssp_host_async(c.handle, rp, col, w, src, d, cfg, stream=s)
+            for c, s in zip(ctxs, streams):
+                s.synchronize()
+                _, st = npb.np_sync(c.handle, stream=s)
+                assert st["error"] == 0
+            for (g, src), (rp, col, w, lv, d) in zip(graphs, bufs):
+                np.testing.assert_array_equal(lv.numpy(), oracle.bfs(g.row_ptr, g.col, src))
+                np.testing.assert_array_equal(d.numpy().view(np.uint32), oracle.sssp(g.row_ptr, g.col, g.w, src))
+                lv.fill_(9)
+                d.fill_(9)
+    finally:
+        ctx2.close()
+
+
 @pytest.mark.parametrize("form", ["tca", "nodp"])
 def test_bezier_host_entry_point(ctx, form):
     ctrl = gen.bezier_curves(700, seed=92)
