@@ -1534,14 +1534,32 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
   const bool static_first = a.scan != 0 && !Body::kOffsets;
   const int warps_total = (int)gridDim.x * ((int)blockDim.x >> 5);
   int own_tile = static_first ? (int)blockIdx.x * ((int)blockDim.x >> 5) + ((int)threadIdx.x >> 5) : -1;
+  // Bodies with output offsets: the CTA's warps take consecutive tiles on one
+  // ticket, combine their tile totals in shared memory, and one warp runs the
+  // look-back for the CTA's group. All groups of a level start at once and each
+  // walks back until a predecessor has its inclusive prefix, so the chain of
+  // look-backs is as many times shorter as the CTA has warps, while every warp
+  // still holds one tile. (Two CTA barriers per group; no other form has any.)
+  __shared__ unsigned s_off[33];
+  __shared__ int s_grp;
+  const int nw = (int)blockDim.x >> 5, wid = (int)threadIdx.x >> 5;
   for (;;) {
-    int tile = own_tile;
-    if (tile < 0) {
-      if (lane == 0) tile = atomicAdd(&st->ticket[slot], 1) + (static_first ? warps_total : 0);
-      tile = __shfl_sync(kFull, tile, 0);
+    int tile = own_tile, grp = 0;
+    if constexpr (Body::kOffsets) {
+      __syncthreads();   // the previous group's shared words are consumed
+      if (threadIdx.x == 0) s_grp = atomicAdd(&st->ticket[slot], 1);
+      __syncthreads();
+      grp = s_grp;
+      if (grp * nw >= ntiles) break;   // uniform over the CTA
+      tile = grp * nw + wid;
+    } else {
+      if (tile < 0) {
+        if (lane == 0) tile = atomicAdd(&st->ticket[slot], 1) + (static_first ? warps_total : 0);
+        tile = __shfl_sync(kFull, tile, 0);
+      }
+      own_tile = -1;   // later tiles come from the ticket
+      if (tile >= ntiles) break;
     }
-    own_tile = -1;   // later tiles come from the ticket
-    if (tile >= ntiles) break;
     const int i = tile * 32 + lane;
     int pid = 0, base = 0, N = 0;
     if (i < count) pid = ids ? __ldcg(&ids[i]) : i;
@@ -1555,15 +1573,30 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
         const int x = __shfl_up_sync(kFull, inc, o);
         if (lane >= o) inc += x;
       }
-      const unsigned t0 = (unsigned)__shfl_sync(kFull, inc, 31);
-      const V3 x = lookback(a.ob_flag, a.ob_agg, a.ob_incl, tile, 0, epoch, V3{t0, 0u, 0u}, st);
-      base = (int)(x.a + (unsigned)(inc - N));
+      if (lane == 31) s_off[wid] = (unsigned)inc;
+      __syncthreads();
+      if (wid == 0) {
+        const unsigned t = lane < nw ? s_off[lane] : 0u;
+        unsigned tin = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned x = __shfl_up_sync(kFull, tin, o);
+          if (lane >= o) tin += x;
+        }
+        const unsigned gtot = __shfl_sync(kFull, tin, 31);
+        const V3 x = lookback(a.ob_flag, a.ob_agg, a.ob_incl, grp, 0, epoch, V3{gtot, 0u, 0u}, st);
+        if (lane < nw) s_off[lane] = x.a + tin - t;   // exclusive prefix of each warp's tile
+        if (lane == 0) s_off[32] = x.a + gtot;
+      }
+      __syncthreads();
+      base = (int)(s_off[wid] + (unsigned)(inc - N));
       if (valid) a.offsets[i] = base;
-      if (tile == ntiles - 1 && lane == 0) a.offsets[count] = (int)(x.a + t0);
+      if ((grp + 1) * nw >= ntiles && threadIdx.x == 0) a.offsets[count] = (int)s_off[32];
       if (valid && (long long)base + N > a.cap) {
         atomicOr(&st->error, kErrCapacity);
         N = 0;
       }
+      if (tile >= ntiles) continue;   // past the level's last tile: only the scan above needed this warp
     }
     const bool launch = FORM == 1 && valid && N >= T;
     const bool serial = valid && !launch && N > 0;
