@@ -710,15 +710,18 @@ def run_ours(args, ws, rank, local):
            "matches_device_result": bool(np.array_equal(e2e_res, res_gpu)),
            "mode": "one waiting call per step (np_*_host), median step"}
     if hasattr(W, "e2e_pipelined"):
-        # the headline end-to-end figure: steps overlap on two contexts; the waiting form
-        # stays beside it
+        # steps overlapped on two contexts (the upload of one with the solve of the other;
+        # the L2 flush of every step is inside this timed region); the faster of the two
+        # host-buffer modes is the end-to-end figure, the other stays beside it
         p_ms, p_res = W.e2e_pipelined(cfg, max(args.e2e_steps, 8), flush, dev)
-        e2e = {"value": units / (p_ms * 1e-3) / 1e9, "unit": W.unit,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": p_ms,
-               "matches_device_result": bool(all(np.array_equal(r, res_gpu) for r in p_res)) and
-               e2e["matches_device_result"],
-               "mode": "stream-ordered calls (np_*_host_async) alternating over 2 contexts and 2 streams",
-               "waiting_call": {k: e2e[k] for k in ("value", "ms_per_step")}}
+        pip = {"value": units / (p_ms * 1e-3) / 1e9, "ms_per_step": p_ms,
+               "mode": "stream-ordered calls (np_*_host_async) alternating over 2 contexts and 2 streams"}
+        wait = {k: e2e[k] for k in ("value", "ms_per_step", "mode")}
+        best, other = (pip, wait) if pip["value"] >= wait["value"] else (wait, pip)
+        e2e.update(best)
+        e2e["matches_device_result"] = bool(e2e["matches_device_result"] and
+                                            all(np.array_equal(r, res_gpu) for r in p_res))
+        e2e["other_mode"] = other
 
     # CPU baseline: the oracle as it stands, one core, bounded sample; also the parity check
     cpu = None
