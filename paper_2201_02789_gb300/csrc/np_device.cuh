@@ -70,6 +70,11 @@
 #ifndef NP_SPREAD_BATCH
 #define NP_SPREAD_BATCH 8
 #endif
+// triangle counting: intersect lists of comparable length by a blocked merge
+// (else by binary searches of the longer list)
+#ifndef NP_TC_MERGE
+#define NP_TC_MERGE 1
+#endif
 // The load that filters a child item before its atomic (level[v] for BFS,
 // dist(v) for SSSP). Only the atomic decides, and a stale value can only be
 // an older one (levels are claimed once, distances only fall), so a filter
@@ -648,6 +653,36 @@ __device__ __forceinline__ bool sorted_contains(const int* a, int n, int key) {
   return lo < n && __ldg(&a[lo]) == key;
 }
 
+// |A ∩ B| of two strictly increasing lists by a blocked merge: per step four
+// entries of each list, all 16 pairs compared, then the block with the smaller
+// maximum moves on (both when the maxima are equal). No pair of blocks is
+// compared twice, and a block is left only when nothing after the other list's
+// current block can equal one of its entries, so each common entry is counted
+// once. Entries past a list's end read as INT_MAX in A and INT_MAX - 1 in B,
+// which match neither each other nor a vertex id. The loop's dependent chain
+// is (na + nb) / 4 loads of consecutive entries (mostly L1 hits), against
+// min(na, nb) binary searches of log2(max) probes each.
+__device__ __forceinline__ unsigned intersect_merge4(const int* A, int na, const int* B, int nb) {
+  unsigned c = 0;
+  int i = 0, j = 0;
+  while (i < na && j < nb) {
+    int a[4], bb[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      a[q] = i + q < na ? __ldg(&A[i + q]) : INT_MAX;
+      bb[q] = j + q < nb ? __ldg(&B[j + q]) : INT_MAX - 1;
+    }
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) c += a[p] == bb[q] ? 1u : 0u;
+    const int amax = a[3], bmax = bb[3];
+    if (amax <= bmax) i += 4;
+    if (bmax <= amax) j += 4;
+  }
+  return c;
+}
+
 struct TcBody {
   static constexpr bool kOffsets = false;
   static constexpr bool kPushes = false;
@@ -689,7 +724,11 @@ struct TcBody {
       const int* walk = walk_u ? nu : nv;
       const int* look = walk_u ? nv : nu;
       const int nw = walk_u ? p[k].n : vn[k], nl = walk_u ? vn[k] : p[k].n;
-      for (int t = 0; t < nw; t++) c += sorted_contains(look, nl, __ldg(&walk[t])) ? 1u : 0u;
+      if (NP_TC_MERGE && nl <= 16 * nw) {
+        c += intersect_merge4(walk, nw, look, nl);   // lists of comparable length
+      } else {
+        for (int t = 0; t < nw; t++) c += sorted_contains(look, nl, __ldg(&walk[t])) ? 1u : 0u;
+      }
     }
     if (c) atomicAdd(&b.acc[blockIdx.x & (kTcSlots - 1)], (unsigned long long)c);
   }
