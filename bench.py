@@ -85,7 +85,7 @@ WORKLOADS = {
 # per-workload values of the aggregated form's knobs, from threshold x cfactor x child-block
 # sweeps on GB300 (the paper also tunes T and CF per benchmark); other workloads use the defaults
 TUNED = {# tessellation: 512-thread parent CTAs make the output-offset look-back groups 16 tiles long
-         "bt64k": dict(parent_block=512, child_block=32, cfactor=4), "tc-rmat17": dict(threshold=8),
+         "bt64k": dict(parent_block=512, child_block=32, cfactor=4), "tc-rmat17": dict(threshold=8, child_block=32, cfactor=1),
          # the 4096-vertex graph is latency-bound: the persistent level loop on 8 CTAs keeps its
          # per-level grid barriers cheap (124 us against 141 us with the graph driver)
          "bfs4k": dict(driver=4, parent_grid=8)}   # driver 4: NP_DRIVER_PERSISTENT
