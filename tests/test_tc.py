@@ -40,6 +40,19 @@ def wheel(k):
     return undirected(k + 1, [(i, (i + 1) % k) for i in range(k)] + [(k, i) for i in range(k)])
 
 
+def clique_with_pendants(k, npend, seed):
+    """K_k plus npend vertices of degree 2, each joined to an adjacent pair of clique
+    vertices (one triangle each): oriented edges between clique vertices join lists of
+    similar length, a pendant's 2-entry list meets a clique vertex's long one."""
+    r = gen.uniform_f64(seed, 901, 0, 2 * npend)
+    edges = list(itertools.combinations(range(k), 2))
+    for i in range(npend):
+        a = int(r[2 * i] * k)
+        b = (a + 1 + int(r[2 * i + 1] * (k - 1))) % k
+        edges += [(k + i, a), (k + i, b)]
+    return undirected(k + npend, edges)
+
+
 def random_graph(n, p, seed):
     u = gen.uniform_f64(seed, 900, 0, n * n).reshape(n, n)
     return undirected(n, [(a, b) for a in range(n) for b in range(a + 1, n) if u[a, b] < p])
@@ -77,6 +90,20 @@ def test_random_vs_brute_force_and_trace(seed):
     g = random_graph(14 + seed, 0.2 + 0.1 * seed, seed)
     t = oracle.triangles(g.row_ptr, g.col)
     assert t == brute(g) == trace_a3(g)
+
+
+def test_lopsided_graph_takes_both_intersection_paths():
+    """The oracle's count on the clique-with-pendants graph is its closed form, and its
+    orientation has edges whose lists differ in length by more than 16x (the binary-search
+    path) as well as edges with lists of similar length (the merge path)."""
+    k, npend = 48, 400
+    u = clique_with_pendants(k, npend, seed=35)
+    assert oracle.triangles(u.row_ptr, u.col) == k * (k - 1) * (k - 2) // 6 + npend
+    dag = gen.oriented_by_degree(u)
+    deg = np.diff(dag.row_ptr.astype(np.int64))
+    src = np.repeat(np.arange(dag.n), deg)
+    lo, hi = np.minimum(deg[src], deg[dag.col]), np.maximum(deg[src], deg[dag.col])
+    assert (hi > 16 * np.maximum(lo, 1)).any() and ((hi <= 16 * lo) & (lo >= 8)).any()
 
 
 def test_orientation_keeps_every_edge_once():
@@ -155,6 +182,8 @@ TC_GRAPHS = {
     "rmat12": lambda: gen.undirected_simple(gen.rmat(12, 16, seed=33, weights=None)),
     "road": lambda: gen.undirected_simple(gen.road_grid(40, 50, seed=6, weights=None)),
     "empty": lambda: undirected(5, []),
+    # both intersection paths: merges between clique lists, binary searches from 2-entry lists
+    "lopsided": lambda: clique_with_pendants(48, 400, seed=35),
 }
 
 
