@@ -1,4 +1,4 @@
-// Kernels of the bfs child body (see np_device.cuh).
+// Kernels of the bfs child body (see np_bodies.cuh).
 #include "np_table.cuh"
 
 namespace nestpar {

@@ -1,4 +1,4 @@
-// Kernels of the triangle-counting child body (see np_device.cuh).
+// Kernels of the triangle-counting child body (see np_bodies.cuh).
 #include "np_table.cuh"
 
 namespace nestpar {
