@@ -45,7 +45,13 @@ struct BfsBody {
 #pragma unroll
     for (int k = 0; k < K; k++) {
       v[k] = f[k].v;
-      cur[k] = valid[k] ? NP_FILTER_LOAD(&b.level[v[k]]) : 0;
+      cur[k] = 0;
+      if (valid[k]) {
+        if (b.vbits)   // -1: not yet visited as far as this SM's copy of the bitmap knows
+          cur[k] = (NP_FILTER_LOAD(&b.vbits[(unsigned)v[k] >> 5]) >> (v[k] & 31)) & 1u ? 0 : -1;
+        else
+          cur[k] = NP_FILTER_LOAD(&b.level[v[k]]);
+      }
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -53,7 +59,11 @@ struct BfsBody {
       if (push[k]) cur[k] = atomicCAS(&b.level[v[k]], -1, b.L + 1);
     }
 #pragma unroll
-    for (int k = 0; k < K; k++) push[k] = push[k] && cur[k] == -1;
+    for (int k = 0; k < K; k++) {
+      push[k] = push[k] && cur[k] == -1;
+      // the claim decides; the bit only lets later visits skip the CAS
+      if (push[k] && b.vbits) atomicOr(&b.vbits[(unsigned)v[k] >> 5], 1u << (v[k] & 31));
+    }
   }
 };
 

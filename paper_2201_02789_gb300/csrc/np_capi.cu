@@ -22,6 +22,8 @@ struct np_ctx {
   unsigned long long* tri = nullptr;  // triangle-counting partial sums [kTcSlots]
   unsigned long long* dtag = nullptr; // packed SSSP state (dist << 32 | tag) of np_sssp / np_sssp_multi
   int64_t dtag_cap = 0;
+  unsigned* vbits = nullptr;          // visited bitmap of np_bfs (32 vertices per word)
+  int64_t vbits_cap = 0;
   // device staging for the *_host entry points
   unsigned char* stage = nullptr;
   size_t stage_bytes = 0;
@@ -42,6 +44,19 @@ np_status ensure_dtag(np_ctx* c, int64_t total) {
   }
   NP_CK(cudaMalloc(&c->dtag, sizeof(unsigned long long) * (size_t)total));
   c->dtag_cap = total;
+  return NP_OK;
+}
+
+np_status ensure_vbits(np_ctx* c, int64_t words) {
+  if (words <= c->vbits_cap) return NP_OK;
+  if (c->vbits) {
+    NP_CK(cudaDeviceSynchronize());
+    cudaFree(c->vbits);
+    c->vbits = nullptr;
+    c->vbits_cap = 0;
+  }
+  NP_CK(cudaMalloc(&c->vbits, sizeof(unsigned) * (size_t)words));
+  c->vbits_cap = words;
   return NP_OK;
 }
 
@@ -75,13 +90,17 @@ np_status solve(np_ctx* c, int kind, const np_csr* g, int src, int* level, unsig
   if (kind == 1) {
     NP_TRY(ensure_dtag(c, g->n));
     a.b.dtag = c->dtag;
+  } else if (NP_BFS_BITMAP) {
+    NP_TRY(ensure_vbits(c, ((int64_t)g->n + 31) / 32));
+    a.b.vbits = c->vbits;
   }
   const int blocks = (int)((g->n + 255) / 256 < 4096 ? (g->n + 255) / 256 : 4096);
   if (c->e.profile) NP_CK(cudaEventRecord(c->e.ev[0], s));
   if (kind == 1)
     init_dtag_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, g->n, src, c->dtag, a.fr0, g->n + 2);
   else
-    init_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, kind, g->n, src, level, dist, a.b.stamp, a.fr0, g->n + 2);
+    init_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, kind, g->n, src, level, dist, a.b.stamp, a.fr0, g->n + 2,
+                                             a.b.vbits);
   NP_CK(cudaGetLastError());
   if (c->e.profile) {
     NP_CK(cudaEventRecord(c->e.ev[3], s));
@@ -320,6 +339,7 @@ np_status np_destroy(np_ctx* c) {
   if (c->ids) cudaFree(c->ids);
   if (c->tri) cudaFree(c->tri);
   if (c->dtag) cudaFree(c->dtag);
+  if (c->vbits) cudaFree(c->vbits);
   engine_release(c->e);
   delete c;
   return NP_OK;

@@ -43,6 +43,11 @@
 #ifndef NP_SPREAD_BATCH
 #define NP_SPREAD_BATCH 8
 #endif
+// np_bfs filters child visits on a visited bitmap instead of level[] (an
+// option: the bit set after each claim costs more than the smaller filter saves)
+#ifndef NP_BFS_BITMAP
+#define NP_BFS_BITMAP 0
+#endif
 // aggregated child blocks of 4 original blocks read edge lists with 16-byte
 // loads (an option: the scalar loads are already coalesced, 128 bytes per warp
 // instruction, and measured faster)
@@ -169,6 +174,10 @@ struct BodyArgs {
   const int* row_ptr;            // triangle counting: row bounds of a child's vertex
   unsigned long long* acc;       // triangle counting: kTcSlots partial counts
   unsigned long long* dtag;      // SSSP, packed form: dist << 32 | tag per vertex
+  // BFS: visited bitmap (bit v set once v is claimed) the children filter on
+  // instead of level[v], or NULL. At 2^20 vertices it is 128 KB, small enough
+  // to stay in an SM's L1, where level[] (4 MB) mostly misses.
+  unsigned* vbits;
 };
 
 struct Args {
