@@ -47,7 +47,7 @@ struct BfsBody {
       v[k] = f[k].v;
       cur[k] = 0;
       if (valid[k]) {
-        if (b.vbits)   // -1: not yet visited as far as this SM's copy of the bitmap knows
+        if (NP_BFS_BITMAP && b.vbits)   // -1: not yet visited as far as this SM's copy of the bitmap knows
           cur[k] = (NP_FILTER_LOAD(&b.vbits[(unsigned)v[k] >> 5]) >> (v[k] & 31)) & 1u ? 0 : -1;
         else
           cur[k] = NP_FILTER_LOAD(&b.level[v[k]]);
@@ -62,7 +62,7 @@ struct BfsBody {
     for (int k = 0; k < K; k++) {
       push[k] = push[k] && cur[k] == -1;
       // the claim decides; the bit only lets later visits skip the CAS
-      if (push[k] && b.vbits) atomicOr(&b.vbits[(unsigned)v[k] >> 5], 1u << (v[k] & 31));
+      if (NP_BFS_BITMAP && push[k] && b.vbits) atomicOr(&b.vbits[(unsigned)v[k] >> 5], 1u << (v[k] & 31));
     }
   }
 };
