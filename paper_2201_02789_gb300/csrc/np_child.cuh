@@ -87,6 +87,14 @@ __device__ __forceinline__ void child_agg_balanced(const BodyArgs& b, const int4
   int j = -1, next_off = 0, off = 0, N = 0, done = 0;
   typename Body::P p{};
   WarpSink sink{b.next, b.next_count};
+  // one hash table per child block (per_cta <= 8: CTAs of 256 threads, cb >= 32)
+  __shared__ int s_tab[NP_TC_HASH ? 8 * Body::kHashSlots : 1];
+  auto sub_sync = [&]() {
+    if (cb == 32)
+      __syncwarp();
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + local), "r"(cb) : "memory");
+  };
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) *s_next = atomicAdd(ticket, per_cta);
@@ -102,6 +110,9 @@ __device__ __forceinline__ void child_agg_balanced(const BodyArgs& b, const int4
         next_off = j + 1 < nrec ? __ldcg(&boff[j + 1]) : 0x7fffffff;
         N = r.z;
         p = Body::parent(b, r.x, r.y, r.z);
+        if constexpr (NP_TC_HASH) {
+          if (per_cta <= 8) Body::build_block(b, p, s_tab + local * Body::kHashSlots, stid, cb, sub_sync);
+        }
       }
       run_coarsened<Body, CF>(b, p, N, B0 - off, cb, stid, sink);
       done++;

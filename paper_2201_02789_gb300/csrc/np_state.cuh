@@ -59,6 +59,13 @@
 #ifndef NP_TC_MERGE
 #define NP_TC_MERGE 1
 #endif
+// triangle counting in the balanced child grid: a child block hashes its
+// parent's out-list in shared memory and probes it from the other list (an
+// option: the per-block table builds and 32 KB of shared memory per CTA cost
+// more than the independent probes gain over the blocked merge)
+#ifndef NP_TC_HASH
+#define NP_TC_HASH 0
+#endif
 // The load that filters a child item before its atomic (level[v] for BFS,
 // dist(v) for SSSP). Only the atomic decides, and a stale value can only be
 // an older one (levels are claimed once, distances only fall), so a filter
