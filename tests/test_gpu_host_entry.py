@@ -90,6 +90,29 @@ def test_async_host_entry_points_on_two_contexts(ctx):
         ctx2.close()
 
 
+def test_async_host_entry_points_pageable_and_degenerate(ctx):
+    """The stream-ordered calls with pageable numpy buffers (the runtime copies synchronously)
+    and on a single vertex without edges; argument errors come back at once."""
+    s = torch.cuda.Stream()
+    g = gen.rmat(12, 8, seed=96)
+    lv = np.full(g.n, 9, np.int32)
+    d = np.full(g.n, 9, np.uint32)
+    npb.np_bfs_host_async(ctx.handle, g.row_ptr, g.col, 5, lv, npb.config("tca"), stream=s)
+    npb.np_sssp_host_async(ctx.handle, g.row_ptr, g.col, g.w, 5, d, npb.config("tca"), stream=s)
+    s.synchronize()
+    assert npb.np_sync(ctx.handle, stream=s)[1]["error"] == 0
+    np.testing.assert_array_equal(lv, oracle.bfs(g.row_ptr, g.col, 5))
+    np.testing.assert_array_equal(d, oracle.sssp(g.row_ptr, g.col, g.w, 5))
+    one = gen.Csr(1, np.zeros(2, np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint32))
+    lv1, d1 = np.full(1, 9, np.int32), np.full(1, 9, np.uint32)
+    npb.np_bfs_host_async(ctx.handle, one.row_ptr, one.col, 0, lv1, npb.config("tca"), stream=s)
+    npb.np_sssp_host_async(ctx.handle, one.row_ptr, one.col, one.w, 0, d1, npb.config("tca"), stream=s)
+    s.synchronize()
+    assert lv1.tolist() == [0] and d1.tolist() == [0]
+    assert npb.np_bfs_host_async(ctx.handle, g.row_ptr, g.col, g.n, lv, npb.config("tca"), stream=s,
+                                 check=False) == npb.NP_ERR_INVALID
+
+
 @pytest.mark.parametrize("form", ["tca", "nodp"])
 def test_bezier_host_entry_point(ctx, form):
     ctrl = gen.bezier_curves(700, seed=92)
