@@ -6,6 +6,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 import torch.multiprocessing as mp
 
@@ -71,3 +72,43 @@ def test_replica_timing_takes_the_slowest_rank():
     assert [o[1] for o in out] == [20.0, 20.0]
     # 2 ranks x 10 steps x 1e6 units in 20 ms = 1.0 G units/s
     assert out[0][2] == pytest.approx(1.0)
+
+
+def test_traffic_is_reported_only_for_the_sources_it_was_taken_on(tmp_path, monkeypatch):
+    """A committed ncu summary counts only while its source hash is the current one."""
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "child_agg_w.md").write_text(
+        "# x\n\n- kernel: child_agg\n- traffic_bytes_per_launch: 1234\n- source_hash: abc\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "source_hash", lambda: "abc")
+    assert bench.ncu_traffic("child_agg", "w") == 1234.0
+    monkeypatch.setattr(bench, "source_hash", lambda: "def")
+    assert bench.ncu_traffic("child_agg", "w") is None
+    assert bench.ncu_traffic("parent_warp", "w") is None   # no summary at all
+
+
+def test_source_hash_follows_every_kernel_source(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2201_02789_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "a.cuh").write_text("int a;\n")
+    (csrc / "notes.txt").write_text("ignored\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.source_hash()
+    (csrc / "notes.txt").write_text("still ignored\n")
+    assert bench.source_hash() == h0
+    (csrc / "b.cu").write_text("int b;\n")
+    h1 = bench.source_hash()
+    assert h1 != h0
+    (csrc / "a.cuh").write_text("int a2;\n")
+    assert bench.source_hash() not in (h0, h1)
+
+
+def test_poisson_arrivals_are_seeded_and_have_the_offered_rate():
+    a = bench.poisson_arrivals(500.0, 20000, seed=5)
+    assert np.array_equal(a, bench.poisson_arrivals(500.0, 20000, seed=5))
+    assert not np.array_equal(a, bench.poisson_arrivals(500.0, 20000, seed=6))
+    gaps = np.diff(np.concatenate([[0.0], a]))
+    assert (gaps > 0).all()
+    # exponential gaps: mean 1/rate, coefficient of variation 1 (20,000 samples: within 3%)
+    assert abs(gaps.mean() * 500.0 - 1.0) < 0.03
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.03
