@@ -11,6 +11,8 @@
   and the offsets-as-exclusive-scan identity.
 * Planted mistakes: plausible errors, made on the CPU in copies of the
   oracle's output or of its formula, must fail these checks.
+* Library routines: BFS levels and SSSP distances equal scipy.sparse.csgraph's
+  unweighted shortest paths and Dijkstra on R-MAT digraphs.
 """
 import itertools
 import math
@@ -265,3 +267,35 @@ def test_planted_count_mistakes_are_caught():
         caught = sum(count(r[:6], mistake) != int(r[6]) for r in rows)
         assert caught >= 1, mistake
     assert all(count(r[:6], None) == int(r[6]) for r in rows)
+
+
+# ------------------------------------------------------ library shortest paths
+
+def _scipy_csr(g, weights):
+    """The graph as a scipy CSR matrix with one entry per (u, v): parallel edges keep their
+    least weight (scipy's graph routines do not take duplicate entries)."""
+    sp = pytest.importorskip("scipy.sparse")
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr.astype(np.int64)))
+    key = src.astype(np.int64) * g.n + g.col
+    order = np.lexsort((weights, key))
+    key, w = key[order], weights[order]
+    first = np.ones(len(key), bool)
+    first[1:] = key[1:] != key[:-1]
+    key, w = key[first], w[first]
+    return sp.csr_matrix((w.astype(np.float64), (key // g.n, key % g.n)), shape=(g.n, g.n))
+
+
+@pytest.mark.parametrize("seed", [41, 42, 43])
+def test_bfs_and_sssp_match_scipy_csgraph(seed):
+    """BFS levels are unweighted shortest-path lengths and SSSP distances Dijkstra's, as
+    scipy.sparse.csgraph computes them, on R-MAT digraphs with parallel edges and hubs."""
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    g = gen.rmat(11, 12, seed=seed)
+    a = _scipy_csr(g, g.w)
+    for src in (0, 17, g.n - 1):
+        hops = csgraph.shortest_path(a, directed=True, unweighted=True, indices=src)
+        want = np.where(np.isinf(hops), -1, hops).astype(np.int64)
+        np.testing.assert_array_equal(oracle.bfs(g.row_ptr, g.col, src).astype(np.int64), want)
+        dist = csgraph.dijkstra(a, directed=True, indices=src)
+        want = np.where(np.isinf(dist), 0xFFFFFFFF, dist).astype(np.int64)
+        np.testing.assert_array_equal(oracle.sssp(g.row_ptr, g.col, g.w, src).astype(np.int64), want)

@@ -234,3 +234,16 @@ def test_gpu_triangles_full_size(ctx):
     for cfg in (npb.config("tca"), npb.config("tca", **bench.TUNED["tc-rmat17"]), npb.config("nodp")):
         got, st = _gpu_count(ctx, dag, cfg)
         assert got == ref and st["error"] == 0
+
+
+def test_oracle_matches_networkx_triangles():
+    """The triangle oracle against networkx's count (per-vertex triangles / 3) on simple
+    undirected R-MAT graphs with hubs."""
+    nx = pytest.importorskip("networkx")
+    for seed in (36, 37):
+        u = gen.undirected_simple(gen.rmat(10, 16, seed=seed, weights=None))
+        G = nx.Graph()
+        G.add_nodes_from(range(u.n))
+        src = np.repeat(np.arange(u.n), np.diff(u.row_ptr))
+        G.add_edges_from(zip(src.tolist(), u.col.tolist()))
+        assert oracle.triangles(u.row_ptr, u.col) == sum(nx.triangles(G).values()) // 3
