@@ -218,6 +218,21 @@ def test_bezier_forms(ctx, form, kw):
     assert st["items"] == ref_off[-1] and st["parents"] == 3000
 
 
+@pytest.mark.parametrize("pb", [64, 128, 512])
+@pytest.mark.parametrize("nc", [1, 33, 3001])
+def test_bezier_offset_groups_of_any_size(ctx, pb, nc):
+    """The output offsets are scanned per CTA group of tiles (2 to 16 warps): ragged curve
+    counts leave the last group partial and some warps past the last tile."""
+    ctrl = gen.bezier_curves(nc, seed=33)
+    ref_off, ref_pts = oracle.bezier(ctrl)
+    for scan in (npb.NP_SCAN_ATOMIC, npb.NP_SCAN_LOOKBACK):
+        status, off, pts, st = bezier(ctx, ctrl, npb.config("tca", parent_block=pb, scan=scan))
+        assert status == npb.NP_OK and st["error"] == 0
+        np.testing.assert_array_equal(off, ref_off)
+        ok, worst = bezier_tolerance_ok(pts[: ref_off[-1]], ref_pts)
+        assert ok, worst
+
+
 def test_bezier_hand_counts_on_gpu(ctx):
     from conftest import read_golden
     rows = read_golden("bezier_counts.txt")["rows"]
