@@ -92,6 +92,26 @@ typedef int32_t np_status;
                                   grid barrier per level, in place of kernel boundaries; barrier waits
                                   are bounded (5 s, then NP_ERR_TIMEOUT) */
 
+/* Where the children of the parents below the threshold run. The paper keeps
+ * them in the parent thread (Section III-A); every form does so except
+ * grid-host aggregation under a graph, chunk or host driver, where `serial`
+ * chooses:
+ *   NP_SERIAL_SPREAD  in the parent kernel (32-parent warp tiles), the items
+ *                     of a warp's parents spread over the warp's lanes;
+ *   NP_SERIAL_BLOCK   in the parent kernel (CTA tiles of parent_block
+ *                     parents), the items of the tile's parents spread over
+ *                     the CTA: the tile's records are staged in shared memory
+ *                     and each thread finds its item's parent by a binary
+ *                     search there;
+ *   NP_SERIAL_PACKED  item by item in the aggregated child grid (threshold at
+ *                     most 1024, else as BLOCK): the parent kernel records
+ *                     them ({parent, start, N, first item}), and each child
+ *                     CTA takes chunks of 1024 items, stages the chunk's
+ *                     records in shared memory and searches there. */
+#define NP_SERIAL_SPREAD 0
+#define NP_SERIAL_PACKED 1
+#define NP_SERIAL_BLOCK 2
+
 typedef struct np_config {
   int32_t variant;       /* NP_VARIANT_* */
   int32_t threshold;     /* launch iff N >= threshold (values <= 1: every parent with N >= 1);
@@ -107,7 +127,8 @@ typedef struct np_config {
   int32_t driver;        /* NP_DRIVER_* (level loop of np_bfs / np_sssp) */
   int32_t unroll;        /* levels per graph chunk or per while-body, 1..16 */
   int32_t parent_grid;   /* persistent parent CTAs; 0 = resident capacity */
-  int32_t reserved[4];   /* must be zero */
+  int32_t serial;        /* NP_SERIAL_*: where the children of parents below the threshold run */
+  int32_t reserved[3];   /* must be zero */
 } np_config;
 
 /* Fills the library defaults: CDP, threshold 32, cfactor 4, grid-host

@@ -8,8 +8,9 @@ namespace nestpar {
 // ------------------------------------------------------------------- bodies
 //
 // A body gives the child count of a parent (count), what every child of a
-// parent shares (parent), the loads of one child item (fetch) and the effect
-// of a batch of K items of one thread (apply_batch), which reports the
+// parent shares (parent, or parent_aux from a staged record that carries the
+// one 32-bit value aux loads for it), the loads of one child item (fetch) and
+// the effect of a batch of K items of one thread (apply_batch), which reports the
 // vertices to append to the next frontier. A batch issues all its loads, then
 // all its atomics, before it uses any of their results, so a thread keeps K
 // memory operations in flight.
@@ -33,6 +34,10 @@ struct BfsBody {
     N = __ldg(&a.row_ptr[u + 1]) - base;
   }
   __device__ static P parent(const BodyArgs& b, int pid, int base, int) { return P{base, pid & ~b.vmask}; }
+  __device__ static unsigned aux(const BodyArgs&, int) { return 0u; }
+  __device__ static P parent_aux(const BodyArgs& b, int pid, int base, int N, unsigned) {
+    return parent(b, pid, base, N);
+  }
   __device__ static P shfl(const P& p, int src) {
     return P{__shfl_sync(kFull, p.base, src), __shfl_sync(kFull, p.qbase, src)};
   }
@@ -89,6 +94,11 @@ struct SsspBody {
   }
   __device__ static P parent(const BodyArgs& b, int pid, int base, int) {
     return P{base, __ldcg(&b.dist[pid]), pid & ~b.vmask};
+  }
+  // what a staged parent record carries besides {parent, base, N}: dist(u)
+  __device__ static unsigned aux(const BodyArgs& b, int pid) { return __ldcg(&b.dist[pid]); }
+  __device__ static P parent_aux(const BodyArgs& b, int pid, int base, int, unsigned du) {
+    return P{base, du, pid & ~b.vmask};
   }
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) {
     return F{p.qbase | __ldg(&b.col[p.base + i]), __ldg(&b.w[p.base + i])};
@@ -207,6 +217,10 @@ struct TcBody {
     N = __ldg(&a.row_ptr[pid + 1]) - base;
   }
   __device__ static P parent(const BodyArgs&, int, int base, int N) { return P{base, N, nullptr, 0}; }
+  __device__ static unsigned aux(const BodyArgs&, int) { return 0u; }
+  __device__ static P parent_aux(const BodyArgs& b, int pid, int base, int N, unsigned) {
+    return parent(b, pid, base, N);
+  }
   __device__ static P shfl(const P& p, int src) {
     return P{__shfl_sync(kFull, p.base, src), __shfl_sync(kFull, p.n, src), nullptr, 0};
   }
@@ -303,6 +317,11 @@ struct Sssp64Body {
   __device__ static P parent(const BodyArgs& b, int pid, int base, int) {
     return P{base, (unsigned)(__ldcg(&b.dtag[pid]) >> 32), pid & ~b.vmask};
   }
+  // what a staged parent record carries besides {parent, base, N}: dist(u)
+  __device__ static unsigned aux(const BodyArgs& b, int pid) { return (unsigned)(__ldcg(&b.dtag[pid]) >> 32); }
+  __device__ static P parent_aux(const BodyArgs& b, int pid, int base, int, unsigned du) {
+    return P{base, du, pid & ~b.vmask};
+  }
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) {
     return F{p.qbase | __ldg(&b.col[p.base + i]), __ldg(&b.w[p.base + i])};
   }
@@ -317,6 +336,7 @@ struct Sssp64Body {
     const unsigned tag = (unsigned)(b.L + 1);
     unsigned long long nd[K], cur[K];
     bool live[K];
+    const bool mirror = NP_SSSP_MIRROR && b.dmirror != nullptr;
 #pragma unroll
     for (int k = 0; k < K; k++) {
       v[k] = f[k].v;
@@ -324,7 +344,10 @@ struct Sssp64Body {
       const unsigned long long s = (unsigned long long)p[k].du + f[k].w;
       nd[k] = ((s >= 0xffffffffull ? 0xfffffffeull : s) << 32) | tag;
 #if NP_SSSP_PRECHECK
-      cur[k] = (valid[k] && live[k]) ? NP_FILTER_LOAD(&b.dtag[v[k]]) : 0ull;
+      if (mirror)
+        cur[k] = (valid[k] && live[k]) ? (unsigned long long)NP_FILTER_LOAD(&b.dmirror[v[k]]) << 32 : 0ull;
+      else
+        cur[k] = (valid[k] && live[k]) ? NP_FILTER_LOAD(&b.dtag[v[k]]) : 0ull;
 #else
       cur[k] = 0xffffffffffffffffull;
 #endif
@@ -335,8 +358,11 @@ struct Sssp64Body {
       if (push[k]) cur[k] = atomicMin(&b.dtag[v[k]], nd[k]);
     }
 #pragma unroll
-    for (int k = 0; k < K; k++)
-      push[k] = push[k] && (nd[k] >> 32) < (cur[k] >> 32) && (unsigned)cur[k] != tag;
+    for (int k = 0; k < K; k++) {
+      const bool lowered = push[k] && (nd[k] >> 32) < (cur[k] >> 32);
+      if (mirror && lowered) atomicMin(&b.dmirror[v[k]], (unsigned)(nd[k] >> 32));
+      push[k] = lowered && (unsigned)cur[k] != tag;
+    }
   }
 };
 
@@ -416,6 +442,10 @@ struct BezierBody {
     const float* c = b.ctrl + 6 * (size_t)pid;
     return P{__ldg(c), __ldg(c + 1), __ldg(c + 2), __ldg(c + 3), __ldg(c + 4), __ldg(c + 5), base,
              (float)(N - 1)};
+  }
+  __device__ static unsigned aux(const BodyArgs&, int) { return 0u; }
+  __device__ static P parent_aux(const BodyArgs& b, int pid, int base, int N, unsigned) {
+    return parent(b, pid, base, N);
   }
   __device__ static P shfl(const P& p, int src) {
     return P{__shfl_sync(kFull, p.x0, src), __shfl_sync(kFull, p.y0, src), __shfl_sync(kFull, p.x1, src),

@@ -90,6 +90,8 @@ np_status solve(np_ctx* c, int kind, const np_csr* g, int src, int* level, unsig
   if (kind == 1) {
     NP_TRY(ensure_dtag(c, g->n));
     a.b.dtag = c->dtag;
+    // the caller's distance array holds the filter copy until the result overwrites it
+    if (NP_SSSP_MIRROR) a.b.dmirror = dist;
   } else if (NP_BFS_BITMAP) {
     NP_TRY(ensure_vbits(c, ((int64_t)g->n + 31) / 32));
     a.b.vbits = c->vbits;
@@ -97,7 +99,7 @@ np_status solve(np_ctx* c, int kind, const np_csr* g, int src, int* level, unsig
   const int blocks = (int)((g->n + 255) / 256 < 4096 ? (g->n + 255) / 256 : 4096);
   if (c->e.profile) NP_CK(cudaEventRecord(c->e.ev[0], s));
   if (kind == 1)
-    init_dtag_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, g->n, src, c->dtag, a.fr0, g->n + 2);
+    init_dtag_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, g->n, src, c->dtag, a.fr0, g->n + 2, a.b.dmirror);
   else
     init_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, kind, g->n, src, level, dist, a.b.stamp, a.fr0, g->n + 2,
                                              a.b.vbits);
@@ -151,9 +153,10 @@ np_status solve_multi(np_ctx* c, int kind, const np_csr* g, int nsrc, const int3
   }
   NP_CK(cudaMemcpyAsync(c->ids, ids.data(), sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, s));
   const BodyKernels& K = kind == 0 ? bfs_kernels() : sssp64_kernels();
-  Plan p = make_plan(K, *cfg);
+  const np_config mcfg = serial_for(*cfg, nsrc, g->m);
+  Plan p = make_plan(K, mcfg);
   Args a;
-  base_args(c->w, *cfg, a);
+  base_args(c->w, mcfg, a);
   a.row_ptr = g->row_ptr;
   a.b.col = g->col_idx;
   a.b.w = g->weights;
@@ -174,7 +177,7 @@ np_status solve_multi(np_ctx* c, int kind, const np_csr* g, int nsrc, const int3
   }
   NP_CK(cudaGetLastError());
   c->e.prof_next_parents = nsrc;
-  NP_TRY(run_levels(c->e, c->w, p, a, *cfg, total, g->n + 2, s));
+  NP_TRY(run_levels(c->e, c->w, p, a, mcfg, total, g->n + 2, s));
   if (kind == 1) {
     dtag_to_dist_kernel<<<blocks_for(total), 256, 0, s>>>(total, c->dtag, dist);
     NP_CK(cudaGetLastError());
@@ -303,6 +306,7 @@ np_status np_config_default(np_config* cfg) {
   cfg->driver = NP_DRIVER_AUTO;
   cfg->unroll = 4;
   cfg->parent_grid = 0;
+  cfg->serial = NP_SERIAL_SPREAD;
   return NP_OK;
 }
 

@@ -453,9 +453,97 @@ __device__ __forceinline__ void agg_totals(const LevelState* st, int L, int mode
     total = __ldcg(&st->agg_blocks[slot]);
   } else {
     const unsigned long long acc = __ldcg(&st->agg_acc[slot]);
-    nrec = (int)(acc >> 40);
-    total = (int)(acc & ((1ull << 40) - 1));
+    nrec = (int)pair_hi(acc);
+    total = (int)pair_lo(acc);
   }
+}
+
+// Totals of the packed serial children of level L (look-back or atomic scan).
+__device__ __forceinline__ void pack_totals(const LevelState* st, int L, int mode, int& nrec, int& nitems) {
+  const int slot = L & 3;
+  if (mode == 1) {
+    nrec = __ldcg(&st->pack_records[slot]);
+    nitems = __ldcg(&st->pack_items[slot]);
+  } else {
+    const unsigned long long acc = __ldcg(&st->pack_acc[slot]);
+    nrec = (int)pair_hi(acc);
+    nitems = (int)pair_lo(acc);
+  }
+}
+
+// Packed serial children: the items of the parents below the threshold,
+// numbered in record order (record j holds items [first_j, first_j + N_j)),
+// run by the CTAs of the aggregated child grid in chunks of kPackItems items
+// taken from the level's pack ticket. Per chunk the CTA stages the records it
+// covers in shared memory: records pfirst[c] .. pfirst[c + 1] (the record
+// holding the next chunk's first item, or the last record), with their first
+// items made chunk-relative and the one value each body needs of its parent
+// (SSSP: dist(u), loaded once per record). Each thread then takes items
+// t = k * blockDim.x + tid, finds the record holding t by a binary search over
+// the staged first items (disaggregation in shared memory, Section II-B), and
+// runs the body on KP items at once. Consecutive items of one record are
+// consecutive edges, so the edge-list loads of a warp stay coalesced.
+#ifndef NP_PACK_BATCH
+#define NP_PACK_BATCH 4
+#endif
+template <class Body>
+__device__ __forceinline__ void child_pack_run(const BodyArgs& b, const int4* prec, const int* pfirst, int nrec,
+                                               int nitems, int* ticket, int* s_stage, int* s_stage_n,
+                                               int* s_stage_base) {
+  // (a parent of more than 16 bytes, the tessellation's control points, takes two per thread)
+  constexpr int KP = sizeof(typename Body::P) > 16 ? 2 : NP_PACK_BATCH;
+  __shared__ int s_chunk;
+  __shared__ int s_first[kPackItems + 1];
+  __shared__ int4 s_rec[kPackItems + 1];
+  const int tid = (int)threadIdx.x, nt = (int)blockDim.x;
+  __syncthreads();   // the previous phase has flushed its staged appends
+  if (tid == 0) *s_stage_n = 0;
+  StageSink sink{b.next, b.next_count, s_stage, s_stage_n};
+  const int nchunks = ceil_div(nitems, kPackItems);
+  for (;;) {
+    if (tid == 0) s_chunk = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int c = s_chunk;
+    if (c >= nchunks) break;   // uniform over the CTA
+    const int c0 = c * kPackItems;
+    const int j0 = __ldcg(&pfirst[c]);
+    const int j1 = c + 1 < nchunks ? __ldcg(&pfirst[c + 1]) : nrec - 1;
+    const int nr = j1 - j0 + 1;   // <= kPackItems + 1: every record has at least one item
+    for (int r = tid; r < nr; r += nt) {
+      const int4 q = __ldcg(&prec[j0 + r]);
+      s_first[r] = q.w - c0;
+      s_rec[r] = make_int4(q.x, q.y, q.z, (int)Body::aux(b, q.x));
+    }
+    __syncthreads();
+    const int here = min(kPackItems, nitems - c0);
+    int top = 1;   // the largest power of two <= nr: the search's first step
+    while (top * 2 <= nr) top *= 2;
+    for (int t0 = 0; t0 < here; t0 += KP * nt) {
+      typename Body::F f[KP];
+      typename Body::P pk[KP];
+      bool v[KP];
+      int idx[KP];
+#pragma unroll
+      for (int k = 0; k < KP; k++) {
+        const int t = t0 + k * nt + tid;
+        v[k] = t < here;
+        // the last staged record whose first item is <= t (s_first[0] <= 0 <= t)
+        int r = 0;
+        for (int step = top; step > 0; step >>= 1)
+          if (r + step < nr && s_first[r + step] <= t) r += step;
+        const int4 q = s_rec[r];
+        idx[k] = t - s_first[r];
+        pk[k] = Body::parent_aux(b, q.x, q.y, q.z, (unsigned)q.w);
+        f[k] = v[k] ? Body::fetch(b, pk[k], idx[k]) : typename Body::F{};
+      }
+      bool pf[KP];
+      int pv[KP];
+      Body::template apply_batch<KP>(b, pk, idx, f, v, pf, pv);
+      if constexpr (Body::kPushes) sink.template push<KP>(pf, pv);
+    }
+    __syncthreads();   // the staged records and the chunk word are free again
+  }
+  if constexpr (Body::kPushes) stage_flush(s_stage, s_stage_n, b.next, b.next_count, s_stage_base);
 }
 
 // Aggregated child grid: a device-launched grid over one segment (mode 0), or
@@ -479,6 +567,36 @@ __global__ void NP_CHILD_AGG_BOUNDS(CF) child_agg(BodyArgs b, AggSeg s) {
   }
   child_agg_run<Body, CF>(b, s.rec, s.boff, nrec, total, s.cb, s.mode != 0, s_stage, &s_stage_n, &s_stage_base,
                           s.mode != 0 ? &b.st->child_ticket[b.L & 3] : nullptr);
+}
+
+}  // namespace nestpar
+
+namespace nestpar {
+
+// The persistent child grid of grid-host aggregation with packed serial
+// children: the aggregated blocks of the launching parents (as child_agg),
+// then chunks of the packed items of the parents below the threshold, which
+// CTAs take from a ticket as they finish their blocks.
+template <class Body, int CF>
+__global__ void NP_CHILD_AGG_BOUNDS(CF) child_agg_pack(BodyArgs b, AggSeg s) {
+  NP_PDL_ENTRY();
+  __shared__ int s_stage[kCtaStage];
+  __shared__ int s_stage_n, s_stage_base;
+  int L = b.L;
+  if (s.level_mode) {
+    L = __ldcg(&b.st->base) + s.k;
+    b.L = L;
+    b.next = (L & 1) ? s.fr0 : s.fr1;
+    b.next_count = &b.st->count[(L + 1) % 3];
+  }
+  int nrec = 0, total = 0, prec_n = 0, pitems = 0;
+  agg_totals(b.st, L, s.mode, nrec, total);
+  pack_totals(b.st, L, s.mode, prec_n, pitems);
+  child_agg_run<Body, CF>(b, s.rec, s.boff, nrec, total, s.cb, true, s_stage, &s_stage_n, &s_stage_base,
+                          &b.st->child_ticket[L & 3]);
+  if (pitems > 0)
+    child_pack_run<Body>(b, s.prec, s.pfirst, prec_n, pitems, &b.st->pack_ticket[L & 3], s_stage, &s_stage_n,
+                         &s_stage_base);
 }
 
 }  // namespace nestpar

@@ -43,6 +43,10 @@ __device__ __forceinline__ void reset_slots(LevelState* st) {
     st->agg_blocks[k] = 0;
     st->agg_acc[k] = 0ull;
     st->child_ticket[k] = 0;
+    st->pack_acc[k] = 0ull;
+    st->pack_records[k] = 0;
+    st->pack_items[k] = 0;
+    st->pack_ticket[k] = 0;
   }
   for (int k = 0; k < S_N; k++) st->s[k] = 0ull;
   st->body_iters = 0;
@@ -162,9 +166,11 @@ __global__ void seed_dtag_kernel(LevelState* st, const int* ids, int nsrc, unsig
 }
 
 __global__ void init_dtag_solve_kernel(LevelState* st, int n, int src, unsigned long long* dtag, int* fr0,
-                                       int max_levels) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+                                       int max_levels, unsigned* mirror) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     dtag[v] = v == src ? 0ull : 0xffffffff00000000ull;
+    if (mirror) mirror[v] = v == src ? 0u : 0xffffffffu;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     fr0[0] = src;
     st->base = 0;
@@ -188,7 +194,7 @@ __global__ void dtag_to_dist_kernel(long long total, const unsigned long long* d
 // (an epoch no solve reaches).
 __global__ void selftest_lookback_kernel(Args a) {
   const unsigned long long epoch = ((__ldcg(&a.st->solve_id) + (1ull << 28)) << 31) | 7ull;
-  lookback(a.lb_flag, a.lb_agg, a.lb_incl, 1, 0, epoch, V3{1u, 0u, 0u}, a.st);
+  lookback(a.lb_flag, a.lb_agg, a.lb_incl, 1, 0, epoch, V4{1u, 0u, 0u, 0u}, a.st);
 }
 
 // A grid barrier that one CTA (blockIdx.x == 1) never reaches.
@@ -248,6 +254,8 @@ Layout layout_for(int64_t parents) {
   L.off_grp_ctr = take(sizeof(int) * L.T);
   L.off_grp_acc = take(sizeof(unsigned long long) * L.T);
   L.off_grp_total = take(sizeof(uint2) * L.T);
+  L.off_prec = take(sizeof(int4) * L.P2);
+  L.off_pfirst = take(sizeof(int) * (L.P2 + 2));
   L.total = o;
   return L;
 }
@@ -339,9 +347,24 @@ np_status check_config(const np_config* cfg) {
   if (cfg->driver < NP_DRIVER_AUTO || cfg->driver > NP_DRIVER_PERSISTENT) return NP_ERR_INVALID;
   if (cfg->unroll < 1 || cfg->unroll > 16) return NP_ERR_INVALID;
   if (cfg->parent_grid < 0) return NP_ERR_INVALID;
-  for (int k = 0; k < 4; k++)
+  if (cfg->serial != NP_SERIAL_SPREAD && cfg->serial != NP_SERIAL_PACKED && cfg->serial != NP_SERIAL_BLOCK)
+    return NP_ERR_INVALID;
+  for (int k = 0; k < 3; k++)
     if (cfg->reserved[k] != 0) return NP_ERR_INVALID;
   return NP_OK;
+}
+
+np_config serial_for(const np_config& cfg, int64_t copies, int64_t m) {
+  np_config c = cfg;
+  if (copies * m >= (int64_t)INT_MAX) c.serial = NP_SERIAL_SPREAD;
+  return c;
+}
+
+int serial_form(const np_config& cfg) {
+  if (cfg.variant != NP_VARIANT_CDP || cfg.granularity != NP_GRAN_GRID_HOST) return NP_SERIAL_SPREAD;
+  // packed children number their items per chunk: a parent meets at most one chunk start
+  if (cfg.serial == NP_SERIAL_PACKED && cfg.threshold > kPackMaxT) return NP_SERIAL_BLOCK;
+  return cfg.serial;
 }
 
 Plan make_plan(const BodyKernels& K, const np_config& cfg) {
@@ -355,8 +378,10 @@ Plan make_plan(const BodyKernels& K, const np_config& cfg) {
     p.mode = M_NODP;
     p.gran = G_NODP;
   } else if (cfg.granularity == NP_GRAN_GRID_HOST) {
-    p.parent = K.parent_grid_host;
-    p.child = K.child_agg[cfi];
+    // (the persistent level loop keeps the warp-tiled parent phase)
+    const int form = serial_form(cfg);
+    p.parent = form == NP_SERIAL_SPREAD ? K.parent_grid_host : K.parent_cta;
+    p.child = form == NP_SERIAL_PACKED ? K.child_agg_pack[cfi] : K.child_agg[cfi];
     p.loop = K.level_loop_agg[cfi];
     p.mode = M_GRID_HOST;
     p.gran = G_GRID_HOST;
@@ -397,6 +422,9 @@ void base_args(const Workspace& w, const np_config& cfg, Args& a) {
   a.group_blocks = cfg.granularity == NP_GRAN_MULTIBLOCK ? cfg.group_blocks : 0;
   a.agg_threshold = (cfg.granularity == NP_GRAN_WARP || cfg.granularity == NP_GRAN_BLOCK) ? cfg.agg_threshold : 0;
   a.scan = cfg.scan;
+  a.pack = serial_form(cfg) == NP_SERIAL_PACKED ? 1 : 0;
+  a.prec = wsp<int4>(w, w.lay.off_prec);
+  a.pfirst = wsp<int>(w, w.lay.off_pfirst);
   a.b.st = w.st;
   a.b.vmask = 0x7fffffff;
   a.count_fixed = -1;
@@ -453,6 +481,9 @@ AggSeg make_seg(const Args& a, const Grids& g, bool level_mode) {
   seg.fr0 = a.fr0;
   seg.fr1 = a.fr1;
   seg.cb = g.cblock;
+  seg.pack = a.pack;
+  seg.prec = a.prec;
+  seg.pfirst = a.pfirst;
   return seg;
 }
 

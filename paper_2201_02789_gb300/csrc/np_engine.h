@@ -57,7 +57,7 @@ struct Plan {
 
 struct Layout {
   size_t off_fr0, off_fr1, off_stamp, off_rec, off_boff, off_lb_flag, off_lb_agg, off_lb_incl, off_ob_flag,
-      off_ob_agg, off_ob_incl, off_grp_ctr, off_grp_acc, off_grp_total, total;
+      off_ob_agg, off_ob_incl, off_grp_ctr, off_grp_acc, off_grp_total, off_prec, off_pfirst, total;
   int64_t P2, T;
 };
 
@@ -106,6 +106,14 @@ T* wsp(const Workspace& w, size_t off) {
 
 int occupancy(Engine& e, const void* fn, int block);
 np_status check_config(const np_config* cfg);
+// Where the children below the threshold run under cfg (NP_SERIAL_*): the
+// configured place for grid-host aggregation (PACKED needs threshold <= 1024,
+// else BLOCK), SPREAD-or-serial-in-thread (the warp-tiled kernels) otherwise.
+int serial_form(const np_config& cfg);
+// The CTA-tiled forms count a tile's or a level's items in 32 bits: a level
+// loop over `copies` traversals of a graph with m edges at once, which could
+// meet 2^31 items or more, takes the warp-tiled parent (SPREAD) instead.
+np_config serial_for(const np_config& cfg, int64_t copies, int64_t m);
 Plan make_plan(const BodyKernels& K, const np_config& cfg);
 // Args of one level loop / pass over workspace `w` (vmask all ones).
 void base_args(const Workspace& w, const np_config& cfg, Args& a);
@@ -163,9 +171,10 @@ __global__ void init_dtag_kernel(long long total, unsigned long long* dtag);
 __global__ void seed_dtag_kernel(LevelState* st, const int* ids, int nsrc, unsigned long long* dtag, int* fr0,
                                  int max_levels);
 __global__ void dtag_to_dist_kernel(long long total, const unsigned long long* dtag, unsigned* dist);
-// Single-source start of the packed form in one kernel (as init_solve_kernel).
+// Single-source start of the packed form in one kernel (as init_solve_kernel);
+// mirror (nullable): the 4-byte distance copy relaxations filter on.
 __global__ void init_dtag_solve_kernel(LevelState* st, int n, int src, unsigned long long* dtag, int* fr0,
-                                       int max_levels);
+                                       int max_levels, unsigned* mirror);
 // *out (+)= the sum of part[0, n) (one block)
 __global__ void sum_u64_kernel(const unsigned long long* part, int n, unsigned long long* out, int accumulate);
 // Sets *bad when a CSR breaks its contract: row_ptr[0] != 0, row_ptr[n] != m,

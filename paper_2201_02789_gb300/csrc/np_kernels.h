@@ -24,6 +24,8 @@ struct BodyKernels {
   const void* child_agg[kNumCF];
   const void* level_loop_nodp;                // level_loop<Body, 0, 1>: persistent no-DP level loop
   const void* level_loop_agg[kNumCF];         // level_loop<Body, 1, cf>: persistent grid-aggregation loop
+  const void* parent_cta;                     // parent_cta<Body>: grid-host, CTA tiles (serial modes BLOCK, PACKED)
+  const void* child_agg_pack[kNumCF];         // child_agg_pack<Body, cf>: the child grid of PACKED
 };
 
 const BodyKernels& bfs_kernels();

@@ -26,7 +26,7 @@ __device__ __forceinline__ void launch_direct(const BodyArgs& b, int pid, int ba
 template <class Body, int CF>
 __device__ __forceinline__ void launch_aggregated(const BodyArgs& b, const int4* rec, const int* boff, int nrec,
                                                   int total, int child_block, unsigned* s_stat, CtaSink& sink) {
-  AggSeg s{rec, boff, nullptr, nullptr, nrec, total, 0, 0, 0, child_block, 0};   // a fixed segment
+  AggSeg s{rec, boff, nullptr, nullptr, nrec, total, 0, 0, 0, child_block, 0, nullptr, nullptr};   // a fixed segment
   child_agg<Body, CF><<<total, child_block, 0, cudaStreamFireAndForget>>>(b, s);
   if (cudaGetLastError() != cudaSuccess) {
     // run the aggregated grid's work in this thread: parent by parent, serially
@@ -64,7 +64,7 @@ __global__ void NP_PARENT_BOUNDS parent_kernel(Args a) {
   if constexpr (GRAN == G_NODP) NP_PDL_ENTRY();
   __shared__ int s_tile;
   __shared__ uint2 s_scan[33];
-  __shared__ V3 s_v3;
+  __shared__ V4 s_v4;
   __shared__ unsigned s_stat[S_N];
   __shared__ int s_q[kStageSlots];
   __shared__ int s_qn, s_qflush, s_qbase;
@@ -110,11 +110,11 @@ __global__ void NP_PARENT_BOUNDS parent_kernel(Args a) {
       unsigned e0, e1, t0, t1;
       block_scan2((unsigned)N, 0u, e0, e1, t0, t1, s_scan);
       if (warp == 0) {
-        V3 x = lookback(a.ob_flag, a.ob_agg, a.ob_incl, tile, 0, epoch, V3{t0, 0u, 0u}, st);
-        if (lane == 0) s_v3 = x;
+        V4 x = lookback(a.ob_flag, a.ob_agg, a.ob_incl, tile, 0, epoch, V4{t0, 0u, 0u, 0u}, st);
+        if (lane == 0) s_v4 = x;
       }
       __syncthreads();
-      const unsigned tile_base = s_v3.a;
+      const unsigned tile_base = s_v4.a;
       __syncthreads();
       base = (int)(tile_base + e0);
       if (valid) a.offsets[i] = base;
@@ -182,15 +182,15 @@ __global__ void NP_PARENT_BOUNDS parent_kernel(Args a) {
         block_scan2(launch ? 1u : 0u, cg, ea, eb, ta, tb, s_scan);
         if (a.scan == 0) {
           if (warp == 0) {
-            V3 x = lookback(a.lb_flag, a.lb_agg, a.lb_incl, tile, first, epoch, V3{ta, tb, 0u}, st);
-            if (lane == 0) s_v3 = x;
+            V4 x = lookback(a.lb_flag, a.lb_agg, a.lb_incl, tile, first, epoch, V4{ta, tb, 0u, 0u}, st);
+            if (lane == 0) s_v4 = x;
           }
         } else if (tid == 0) {
-          const unsigned long long old = atomicAdd(&a.grp_acc[g], ((unsigned long long)ta << 40) | tb);
-          s_v3 = V3{(unsigned)(old >> 40), (unsigned)(old & ((1ull << 40) - 1)), 0u};
+          const unsigned long long old = atomicAdd(&a.grp_acc[g], pair_word(ta, tb));
+          s_v4 = V4{pair_hi(old), pair_lo(old), 0u, 0u};
         }
         __syncthreads();
-        const V3 x = s_v3;
+        const V4 x = s_v4;
         const int seg = first * PB;
         if (launch) {
           a.rec[seg + x.a + ea] = make_int4(pid, base, N, 0);
@@ -211,8 +211,8 @@ __global__ void NP_PARENT_BOUNDS parent_kernel(Args a) {
                 nblk = t.y;
               } else {
                 const unsigned long long t = atomicExch(&a.grp_acc[g], 0ull);
-                nrec = (unsigned)(t >> 40);
-                nblk = (unsigned)(t & ((1ull << 40) - 1));
+                nrec = pair_hi(t);
+                nblk = pair_lo(t);
               }
               a.grp_ctr[g] = 0;
               if (nrec > 0) launch_aggregated<Body, CF>(b, a.rec + seg, a.boff + seg, (int)nrec, (int)nblk, CB, s_stat, sink);
@@ -331,7 +331,7 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
           if (lane >= o) tin += x;
         }
         const unsigned gtot = __shfl_sync(kFull, tin, 31);
-        const V3 x = lookback(a.ob_flag, a.ob_agg, a.ob_incl, grp, 0, epoch, V3{gtot, 0u, 0u}, st);
+        const V4 x = lookback(a.ob_flag, a.ob_agg, a.ob_incl, grp, 0, epoch, V4{gtot, 0u, 0u, 0u}, st);
         if (lane < nw) s_off[lane] = x.a + tin - t;   // exclusive prefix of each warp's tile
         if (lane == 0) s_off[32] = x.a + gtot;
       }
@@ -363,15 +363,15 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
       }
       const unsigned ta = __popc(lm), tb = __shfl_sync(kFull, inc, 31);
       const unsigned ea = __popc(lm & lanemask_lt()), eb = inc - cg;
-      V3 x{0u, 0u, 0u};
+      V4 x{0u, 0u, 0u, 0u};
       if (a.scan == 0) {
-        x = lookback(a.lb_flag, a.lb_agg, a.lb_incl, tile, 0, epoch, V3{ta, tb, 0u}, st);
+        x = lookback(a.lb_flag, a.lb_agg, a.lb_incl, tile, 0, epoch, V4{ta, tb, 0u, 0u}, st);
       } else if (ta > 0) {
         // (a tile without launching parents needs no slots: no atomic round trip)
         unsigned long long old = 0ull;
-        if (lane == 0) old = atomicAdd(&st->agg_acc[slot], ((unsigned long long)ta << 40) | tb);
+        if (lane == 0) old = atomicAdd(&st->agg_acc[slot], pair_word(ta, tb));
         old = __shfl_sync(kFull, old, 0);
-        x = V3{(unsigned)(old >> 40), (unsigned)(old & ((1ull << 40) - 1)), 0u};
+        x = V4{pair_hi(old), pair_lo(old), 0u, 0u};
       }
       if (launch) {
         a.rec[x.a + ea] = make_int4(pid, base, N, 0);
@@ -456,6 +456,203 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
     }
   }
   if constexpr (Body::kPushes) stage_flush(s_stage, s_stage_n, b.next, b.next_count, s_stage_base);
+  if (lane == 0) {
+    add_stat(st, S_PARENTS, n_par);
+    add_stat(st, S_ITEMS, n_items);
+    add_stat(st, S_SERIAL, n_serial);
+    add_stat(st, S_LAUNCHP, n_launch);
+    add_stat(st, S_CITEMS, n_citems);
+  }
+}
+
+// --------------------------------------- parent side, CTA-tiled grid-host
+//
+// The parent kernel of grid-host aggregation with CTA tiles. Per tile of
+// blockDim.x parents: child counts, one CTA scan of four counters (launching
+// parents, their coarsened blocks, parents below the threshold, their items),
+// then the paper's packed 64-bit atomic per counter pair (or one decoupled
+// look-back over the tiles, which keeps records in parent order):
+//   N >= T     rec / boff, for the aggregated child grid;
+//   0 < N < T  serialised children (Section III-A), in one of two ways:
+//     a.pack == 0  they stay in this kernel, spread over the CTA: the tile's
+//                  parents below the threshold are staged in shared memory
+//                  ({parent, start, N, the value the body stages}, first item
+//                  from the scan) and every thread takes items
+//                  t = k * blockDim.x + tid, finds its parent by a binary
+//                  search over the staged first items and runs the body on
+//                  NP_CTA_SPREAD_BATCH items at once;
+//     a.pack == 1  they go packed to the child grid: prec = {parent, start, N,
+//                  first item} and pfirst[k] = that record when it holds item
+//                  k * kPackItems (N < kPackItems: at most one chunk start).
+// Capped at 48 registers: five 256-thread CTAs per SM.
+#ifndef NP_CTA_PARENT_MAXREG
+#define NP_CTA_PARENT_MAXREG 48
+#endif
+#ifndef NP_CTA_SPREAD_BATCH
+#define NP_CTA_SPREAD_BATCH 4
+#endif
+template <class Body>
+__global__ void __maxnreg__(NP_CTA_PARENT_MAXREG) parent_cta(Args a) {
+  NP_PDL_ENTRY();
+  // items per thread per round of the CTA-wide serial loop (the tessellation's
+  // 32-byte parent takes two)
+  constexpr int KS = sizeof(typename Body::P) > 16 ? 2 : NP_CTA_SPREAD_BATCH;
+  __shared__ int s_tile;
+  __shared__ uint4 s_scan[33];
+  __shared__ uint2 s_scan2[33];
+  __shared__ V4 s_x;
+  __shared__ int s_first[kMaxParentBlock];
+  __shared__ int4 s_rec[kMaxParentBlock];
+  __shared__ int s_stage[Body::kPushes ? kCtaStage : 1];
+  __shared__ int s_stage_n, s_stage_base;
+  const int tid = (int)threadIdx.x, PB = (int)blockDim.x, lane = tid & 31, warp = tid >> 5;
+  LevelState* st = a.st;
+  const bool fixed = a.count_fixed >= 0;
+  int L = a.L_fixed, count = a.count_fixed;
+  if (!fixed) level_of(st, a.k, L, count);
+  if (!fixed && blockIdx.x == 0 && tid == 0) level_open(st, L, count);
+  if (count <= 0) return;   // uniform over the grid
+  const int ntiles = ceil_div(count, PB);
+  if ((int)blockIdx.x >= ntiles) return;
+  const unsigned long long epoch = level_epoch(st, L);
+  const int slot = L & 3;
+  const int* ids = fixed ? a.ids : ((L & 1) ? a.fr1 : a.fr0);
+  BodyArgs b = a.b;
+  b.L = L;
+  b.next = fixed ? a.next_ovr : ((L & 1) ? a.fr0 : a.fr1);
+  b.next_count = fixed ? a.next_count_ovr : &st->count[(L + 1) % 3];
+  const int T = a.threshold < 1 ? 1 : a.threshold;
+  const int CB = a.child_block;
+  if (tid == 0) s_stage_n = 0;
+  StageSink sink{b.next, b.next_count, s_stage, &s_stage_n};
+  // Without look-back waits no tile waits on another, so a CTA's first tile is
+  // its own index and only later tiles come from the ticket.
+  const bool static_first = a.scan != 0 && !Body::kOffsets;
+  int own = static_first ? (int)blockIdx.x : -1;
+  unsigned n_par = 0, n_serial = 0, n_launch = 0;
+  unsigned long long n_items = 0, n_citems = 0;
+  for (;;) {
+    int tile = own;
+    if (tile < 0) {
+      // s_tile is read before the next write: thread 0 rewrites it only after
+      // the CTA barriers of this tile's scan
+      if (tid == 0) s_tile = atomicAdd(&st->ticket[slot], 1) + (static_first ? (int)gridDim.x : 0);
+      __syncthreads();
+      tile = s_tile;
+    }
+    own = -1;
+    if (tile >= ntiles) break;   // uniform over the CTA
+    const int i = tile * PB + tid;
+    int pid = 0, base = 0, N = 0;
+    if (i < count) pid = ids ? __ldcg(&ids[i]) : i;
+    const bool valid = i < count && pid >= 0;   // frontier slots padded with -1 hold no parent
+    if (valid) Body::count(a, pid, base, N);
+    if constexpr (Body::kOffsets) {
+      // output offsets: exclusive scan of N over all parents, in parent order
+      unsigned e0, e1, t0, t1;
+      block_scan2((unsigned)N, 0u, e0, e1, t0, t1, s_scan2);
+      if (warp == 0) {
+        const V4 x = lookback(a.ob_flag, a.ob_agg, a.ob_incl, tile, 0, epoch, V4{t0, 0u, 0u, 0u}, st);
+        if (lane == 0) s_x = x;
+      }
+      __syncthreads();
+      const unsigned tile_base = s_x.a;
+      __syncthreads();
+      base = (int)(tile_base + e0);
+      if (valid) a.offsets[i] = base;
+      if (tile == ntiles - 1 && tid == 0) a.offsets[count] = (int)(tile_base + t0);
+      if (valid && (long long)base + N > a.cap) {
+        atomicOr(&st->error, kErrCapacity);
+        N = 0;
+      }
+    }
+    const bool launch = valid && N >= T;
+    const bool small = valid && !launch && N > 0;
+    const unsigned cg = launch ? (unsigned)ceil_div(ceil_div(N, CB), a.cfactor) : 0u;
+    uint4 ex, tot;
+    block_scan4(make_uint4(launch ? 1u : 0u, cg, small ? 1u : 0u, small ? (unsigned)N : 0u), ex, tot, s_scan);
+    // only packed children need places beyond this tile
+    const V4 mine{tot.x, tot.y, a.pack ? tot.z : 0u, a.pack ? tot.w : 0u};
+    if (a.scan == 0) {
+      if (warp == 0) {
+        const V4 x = lookback(a.lb_flag, a.lb_agg, a.lb_incl, tile, 0, epoch, mine, st);
+        if (lane == 0) s_x = x;
+      }
+    } else if (tid == 0) {
+      // (no atomic round trip for a counter pair the tile leaves at zero)
+      unsigned long long o1 = 0ull, o2 = 0ull;
+      if (mine.a) o1 = atomicAdd(&st->agg_acc[slot], pair_word(mine.a, mine.b));
+      if (mine.c) o2 = atomicAdd(&st->pack_acc[slot], pair_word(mine.c, mine.d));
+      s_x = V4{pair_hi(o1), pair_lo(o1), pair_hi(o2), pair_lo(o2)};
+    }
+    if (small && !a.pack) {
+      s_first[ex.z] = (int)ex.w;
+      s_rec[ex.z] = make_int4(pid, base, N, (int)Body::aux(b, pid));
+    }
+    __syncthreads();
+    const V4 x = s_x;
+    if (launch) {
+      a.rec[x.a + ex.x] = make_int4(pid, base, N, 0);
+      a.boff[x.a + ex.x] = (int)(x.b + ex.y);
+    }
+    if (small && a.pack) {
+      const int j = (int)(x.c + ex.z);
+      const int first = (int)(x.d + ex.w);
+      a.prec[j] = make_int4(pid, base, N, first);
+      const int k = ceil_div(first, kPackItems);   // the first chunk start at or after `first`
+      if (k * kPackItems < first + N) a.pfirst[k] = j;
+    }
+    if (a.scan == 0 && tile == ntiles - 1 && tid == 0) {
+      st->agg_records[slot] = (int)(x.a + tot.x);
+      st->agg_blocks[slot] = (int)(x.b + tot.y);
+      st->pack_records[slot] = (int)(x.c + mine.c);
+      st->pack_items[slot] = (int)(x.d + mine.d);
+    }
+    n_par += valid ? 1u : 0u;
+    n_items += (unsigned)N;
+    n_serial += small ? 1u : 0u;
+    n_launch += launch ? 1u : 0u;
+    n_citems += launch ? (unsigned)N : 0u;
+    if (!a.pack && tot.w > 0) {   // uniform over the CTA
+      const int nr = (int)tot.z, items = (int)tot.w;
+      int top = 1;   // the largest power of two <= nr: the search's first step
+      while (top * 2 <= nr) top *= 2;
+      for (int t0 = 0; t0 < items; t0 += KS * PB) {
+        typename Body::F f[KS];
+        typename Body::P pk[KS];
+        bool v[KS];
+        int idx[KS];
+#pragma unroll
+        for (int k = 0; k < KS; k++) {
+          const int t = t0 + k * PB + tid;
+          v[k] = t < items;
+          // the last staged parent whose first item is <= t (s_first[0] = 0)
+          int r = 0;
+          for (int step = top; step > 0; step >>= 1)
+            if (r + step < nr && s_first[r + step] <= t) r += step;
+          const int4 q = s_rec[r];
+          idx[k] = t - s_first[r];
+          pk[k] = Body::parent_aux(b, q.x, q.y, q.z, (unsigned)q.w);
+          f[k] = v[k] ? Body::fetch(b, pk[k], idx[k]) : typename Body::F{};
+        }
+        bool pf[KS];
+        int pv[KS];
+        Body::template apply_batch<KS>(b, pk, idx, f, v, pf, pv);
+        if constexpr (Body::kPushes) sink.template push<KS>(pf, pv);
+      }
+    }
+    // s_x, s_first and s_rec are rewritten only after the next tile's scan
+    // barriers: no barrier here
+  }
+  if constexpr (Body::kPushes) stage_flush(s_stage, &s_stage_n, b.next, b.next_count, &s_stage_base);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n_par += __shfl_xor_sync(kFull, n_par, o);
+    n_items += __shfl_xor_sync(kFull, n_items, o);
+    n_serial += __shfl_xor_sync(kFull, n_serial, o);
+    n_launch += __shfl_xor_sync(kFull, n_launch, o);
+    n_citems += __shfl_xor_sync(kFull, n_citems, o);
+  }
   if (lane == 0) {
     add_stat(st, S_PARENTS, n_par);
     add_stat(st, S_ITEMS, n_items);

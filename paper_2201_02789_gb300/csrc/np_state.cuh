@@ -84,6 +84,11 @@
 #ifndef NP_SSSP_PRECHECK
 #define NP_SSSP_PRECHECK 1
 #endif
+// 1: whole SSSP solves filter relaxations on a 4-byte distance copy kept in
+// the caller's output array during the solve (BodyArgs::dmirror)
+#ifndef NP_SSSP_MIRROR
+#define NP_SSSP_MIRROR 0
+#endif
 #ifdef NP_CHILD_MAXREG
 #define NP_CHILD_BOUNDS __maxnreg__(NP_CHILD_MAXREG)
 #define NP_CHILD_AGG_BOUNDS(CF) __maxnreg__(NP_CHILD_MAXREG)
@@ -102,6 +107,11 @@
 namespace nestpar {
 
 constexpr int kMaxParentBlock = 512;
+// Packed serial children: the child grid takes them in chunks of kPackItems
+// items (a CTA stages the chunk's parent records in shared memory); a parent
+// has fewer than kPackMaxT items, so it meets at most one chunk start.
+constexpr int kPackItems = 1024;
+constexpr int kPackMaxT = kPackItems;
 constexpr unsigned kErrLaunch = 1u, kErrTimeout = 2u, kErrCapacity = 4u;
 constexpr int kSpinLimit = 1 << 21;   // polls before a look-back wait gives up
 constexpr unsigned kFull = 0xffffffffu;
@@ -124,13 +134,22 @@ struct __align__(16) LevelState {
   int ticket[4];                 // slot L % 4: next parent tile of level L
   int agg_records[4];            // slot L % 4: grid-host totals, look-back scan
   int agg_blocks[4];
-  unsigned long long agg_acc[4]; // slot L % 4: grid-host totals, atomic scan (parents << 40 | blocks)
+  unsigned long long agg_acc[4]; // slot L % 4: grid-host totals, atomic scan (pair_word(parents, blocks))
   unsigned long long s[S_N];     // counters (np_stats)
   int body_iters;                // conditional-while iterations of this solve (bounded)
   int pad;
   int child_ticket[4];           // slot L % 4: next chunk of aggregated blocks (balanced bodies)
   unsigned bar_count;            // grid barrier of the persistent level loop: arrivals
   unsigned bar_gen;              // and generation
+  // Packed serial children (grid-host form): per slot L % 4, the records and
+  // items of the parents below the threshold, as the atomic scan's packed
+  // accumulator (pair_word(records, items)) or the look-back scan's totals, and
+  // the ticket of the child grid's item chunks.
+  unsigned long long pack_acc[4];
+  int pack_records[4];
+  int pack_items[4];
+  int pack_ticket[4];
+  int pad2[4];
 };
 
 __device__ __forceinline__ unsigned long long level_epoch(const LevelState* st, int L) {
@@ -154,6 +173,10 @@ __device__ __forceinline__ void level_open(LevelState* st, int L, int count) {
   st->agg_blocks[s2] = 0;
   st->agg_acc[s2] = 0ull;
   st->child_ticket[s2] = 0;
+  st->pack_acc[s2] = 0ull;
+  st->pack_records[s2] = 0;
+  st->pack_items[s2] = 0;
+  st->pack_ticket[s2] = 0;
   st->count[(L + 2) % 3] = 0;
   if (count > 0) {
     atomicAdd(&st->s[S_LEVELS], 1ull);
@@ -185,6 +208,11 @@ struct BodyArgs {
   // instead of level[v], or NULL. At 2^20 vertices it is 128 KB, small enough
   // to stay in an SM's L1, where level[] (4 MB) mostly misses.
   unsigned* vbits;
+  // SSSP, packed form: a 4-byte copy of each distance that relaxations filter
+  // on instead of the 8-byte packed word, or NULL. It is lowered after every
+  // 64-bit atomicMin that lowers the distance, so it is never below the
+  // distance: a relaxation it rejects could not have lowered it either.
+  unsigned* dmirror;
 };
 
 struct Args {
@@ -218,7 +246,12 @@ struct Args {
   int agg_threshold;
   int scan;                      // 0 look-back, 1 atomic
   int k;                         // level mode: position in the graph body (level = base + k)
-  int pad;
+  int pack;                      // 1: children below the threshold go packed to the child grid
+  // packed serial children: one record {parent, row start or output offset,
+  // N, first item} per parent below the threshold, and per chunk of
+  // kPackItems items the record holding the chunk's first item
+  int4* prec;
+  int* pfirst;
 };
 
 struct AggSeg {
@@ -232,7 +265,9 @@ struct AggSeg {
   int k;                         // level mode: position in the graph body
   int level_mode;                // 1: take L, next and next_count from the level state
   int cb;                        // child block size; a CTA hosts blockDim.x / cb child blocks
-  int pad;
+  int pack;                      // 1: also run the packed serial children (prec, pfirst)
+  const int4* prec;
+  const int* pfirst;
 };
 
 // ---------------------------------------------------------------- primitives
@@ -252,16 +287,31 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 }
 __host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
-struct V3 {
-  unsigned a, b, c;
+// The aggregation atomic adds two counters at once in one 64-bit word (the
+// paper packs parents and blocks). Each gets 32 bits here: per level both stay
+// below 2^31 (a level has fewer than 2^31 parents and, for the counters this
+// word carries, fewer than 2^31 children or blocks), whereas a 24-bit parent
+// field overflows in one level of a large batch group (tens of millions of
+// parents below the threshold), and a wrapped count misplaces records.
+__device__ __forceinline__ unsigned long long pair_word(unsigned hi, unsigned lo) {
+  return ((unsigned long long)hi << 32) | lo;
+}
+__device__ __forceinline__ unsigned pair_hi(unsigned long long w) { return (unsigned)(w >> 32); }
+__device__ __forceinline__ unsigned pair_lo(unsigned long long w) { return (unsigned)(w & 0xffffffffull); }
+
+// Up to four counters scanned together (records, blocks, and for packed
+// serial children their records and items).
+struct V4 {
+  unsigned a, b, c, d;
 };
-__device__ __forceinline__ V3 v3add(V3 x, V3 y) { return V3{x.a + y.a, x.b + y.b, x.c + y.c}; }
-__device__ __forceinline__ V3 warp_sum3(V3 v) {
+__device__ __forceinline__ V4 v4add(V4 x, V4 y) { return V4{x.a + y.a, x.b + y.b, x.c + y.c, x.d + y.d}; }
+__device__ __forceinline__ V4 warp_sum4(V4 v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     v.a += __shfl_xor_sync(kFull, v.a, o);
     v.b += __shfl_xor_sync(kFull, v.b, o);
     v.c += __shfl_xor_sync(kFull, v.c, o);
+    v.d += __shfl_xor_sync(kFull, v.d, o);
   }
   return v;
 }
@@ -271,22 +321,22 @@ __device__ __forceinline__ V3 warp_sum3(V3 v) {
 // Flags hold (epoch << 2) | status, status 1 = aggregate published,
 // 2 = inclusive prefix published. Waits are bounded: on expiry the error word
 // gets kErrTimeout and the wait is abandoned (result then wrong, never a hang).
-__device__ inline V3 lookback(unsigned long long* flag, uint4* agg, uint4* incl, int tile, int first,
-                       unsigned long long epoch, V3 mine, LevelState* st) {
+__device__ inline V4 lookback(unsigned long long* flag, uint4* agg, uint4* incl, int tile, int first,
+                       unsigned long long epoch, V4 mine, LevelState* st) {
   const int lane = threadIdx.x & 31;
   const unsigned long long fA = (epoch << 2) | 1ull, fP = (epoch << 2) | 2ull;
   if (tile == first) {
     if (lane == 0) {
-      incl[tile] = make_uint4(mine.a, mine.b, mine.c, 0u);
+      incl[tile] = make_uint4(mine.a, mine.b, mine.c, mine.d);
       st_release_u64(&flag[tile], fP);
     }
-    return V3{0, 0, 0};
+    return V4{0, 0, 0, 0};
   }
   if (lane == 0) {
-    agg[tile] = make_uint4(mine.a, mine.b, mine.c, 0u);
+    agg[tile] = make_uint4(mine.a, mine.b, mine.c, mine.d);
     st_release_u64(&flag[tile], fA);
   }
-  V3 excl{0, 0, 0};
+  V4 excl{0, 0, 0, 0};
   int j = tile - 1;
   for (;;) {
     const int idx = j - lane;
@@ -311,21 +361,21 @@ __device__ inline V3 lookback(unsigned long long* flag, uint4* agg, uint4* incl,
       }
     }
     const bool isP = (f & 3ull) == 2ull;
-    V3 v{0, 0, 0};
+    V4 v{0, 0, 0, 0};
     if (in && !timed_out) {
       uint4 x = __ldcg(isP ? &incl[idx] : &agg[idx]);
-      v = V3{x.x, x.y, x.z};
+      v = V4{x.x, x.y, x.z, x.w};
     }
     const unsigned pm = __ballot_sync(kFull, isP);
     const int stop = pm ? __ffs(pm) - 1 : 31;
-    if (lane > stop) v = V3{0, 0, 0};
-    excl = v3add(excl, warp_sum3(v));
+    if (lane > stop) v = V4{0, 0, 0, 0};
+    excl = v4add(excl, warp_sum4(v));
     if (pm) break;
     j -= 32;
   }
   if (lane == 0) {
-    V3 inc = v3add(excl, mine);
-    incl[tile] = make_uint4(inc.a, inc.b, inc.c, 0u);
+    V4 inc = v4add(excl, mine);
+    incl[tile] = make_uint4(inc.a, inc.b, inc.c, inc.d);
     st_release_u64(&flag[tile], fP);
   }
   return excl;
@@ -367,6 +417,49 @@ __device__ __forceinline__ void block_scan2(unsigned a, unsigned b, unsigned& ea
   eb = wp.y + ib - b;
   ta = s[32].x;
   tb = s[32].y;
+  __syncthreads();
+}
+
+// Exclusive scan of four counters over the CTA (one warp scan, one scan of the
+// warp totals): returns this thread's exclusive values and the CTA totals (in
+// all threads). Uses s[0..32].
+__device__ __forceinline__ void block_scan4(uint4 v, uint4& ex, uint4& tot, uint4* s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint4 in = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned x0 = __shfl_up_sync(kFull, in.x, o), x1 = __shfl_up_sync(kFull, in.y, o);
+    const unsigned x2 = __shfl_up_sync(kFull, in.z, o), x3 = __shfl_up_sync(kFull, in.w, o);
+    if (lane >= o) {
+      in.x += x0;
+      in.y += x1;
+      in.z += x2;
+      in.w += x3;
+    }
+  }
+  if (lane == 31) s[warp] = in;
+  __syncthreads();
+  if (warp == 0) {
+    const uint4 t = lane < nw ? s[lane] : make_uint4(0u, 0u, 0u, 0u);
+    uint4 x = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y0 = __shfl_up_sync(kFull, x.x, o), y1 = __shfl_up_sync(kFull, x.y, o);
+      const unsigned y2 = __shfl_up_sync(kFull, x.z, o), y3 = __shfl_up_sync(kFull, x.w, o);
+      if (lane >= o) {
+        x.x += y0;
+        x.y += y1;
+        x.z += y2;
+        x.w += y3;
+      }
+    }
+    if (lane < nw) s[lane] = make_uint4(x.x - t.x, x.y - t.y, x.z - t.z, x.w - t.w);   // exclusive warp prefix
+    if (lane == 31) s[32] = x;                                                          // CTA total
+  }
+  __syncthreads();
+  const uint4 wp = s[warp];
+  ex = make_uint4(wp.x + in.x - v.x, wp.y + in.y - v.y, wp.z + in.z - v.z, wp.w + in.w - v.w);
+  tot = s[32];
   __syncthreads();
 }
 

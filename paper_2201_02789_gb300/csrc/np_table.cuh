@@ -40,6 +40,12 @@ inline BodyKernels make_table() {
   t.level_loop_agg[2] = (const void*)level_loop<Body, 1, 4>;
   t.level_loop_agg[3] = (const void*)level_loop<Body, 1, 8>;
   t.level_loop_agg[4] = (const void*)level_loop<Body, 1, 16>;
+  t.parent_cta = (const void*)parent_cta<Body>;
+  t.child_agg_pack[0] = (const void*)child_agg_pack<Body, 1>;
+  t.child_agg_pack[1] = (const void*)child_agg_pack<Body, 2>;
+  t.child_agg_pack[2] = (const void*)child_agg_pack<Body, 4>;
+  t.child_agg_pack[3] = (const void*)child_agg_pack<Body, 8>;
+  t.child_agg_pack[4] = (const void*)child_agg_pack<Body, 16>;
   return t;
 }
 

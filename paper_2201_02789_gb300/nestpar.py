@@ -24,6 +24,7 @@ NP_VARIANT_NODP, NP_VARIANT_CDP = 0, 1
 NP_GRAN_NONE, NP_GRAN_WARP, NP_GRAN_BLOCK, NP_GRAN_MULTIBLOCK, NP_GRAN_GRID_DEVICE, NP_GRAN_GRID_HOST = range(6)
 NP_SCAN_LOOKBACK, NP_SCAN_ATOMIC = 0, 1
 NP_DRIVER_AUTO, NP_DRIVER_HOST, NP_DRIVER_CHUNK, NP_DRIVER_WHILE, NP_DRIVER_PERSISTENT = range(5)
+NP_SERIAL_SPREAD, NP_SERIAL_PACKED, NP_SERIAL_BLOCK = 0, 1, 2
 NP_COUNT_CSR_DEGREE, NP_COUNT_BEZIER = 0, 1
 NP_BODY_BFS_VISIT, NP_BODY_SSSP_RELAX, NP_BODY_BEZIER_EVAL, NP_BODY_TRIANGLES = 0, 1, 2, 3
 NP_TRI_SLOTS = 256
@@ -47,7 +48,7 @@ class np_config(ctypes.Structure):
                 ("agg_threshold", ctypes.c_int32), ("child_block", ctypes.c_int32),
                 ("parent_block", ctypes.c_int32), ("scan", ctypes.c_int32), ("driver", ctypes.c_int32),
                 ("unroll", ctypes.c_int32), ("parent_grid", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("serial", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
     def replace(self, **kw) -> "np_config":
         c = np_config()

@@ -54,7 +54,10 @@ def form_grid():
              ("mb1", npb.NP_GRAN_MULTIBLOCK, {"group_blocks": 1}),
              ("mb3", npb.NP_GRAN_MULTIBLOCK, {"group_blocks": 3}),
              ("mb8", npb.NP_GRAN_MULTIBLOCK, {"group_blocks": 8}),
-             ("griddev", npb.NP_GRAN_GRID_DEVICE, {}), ("gridhost", npb.NP_GRAN_GRID_HOST, {})]
+             ("griddev", npb.NP_GRAN_GRID_DEVICE, {}),
+             ("gridhost-spread", npb.NP_GRAN_GRID_HOST, {"serial": npb.NP_SERIAL_SPREAD}),
+             ("gridhost-block", npb.NP_GRAN_GRID_HOST, {"serial": npb.NP_SERIAL_BLOCK}),
+             ("gridhost-packed", npb.NP_GRAN_GRID_HOST, {"serial": npb.NP_SERIAL_PACKED})]
     for gname, gran, extra in grans:
         scans = ([("", npb.NP_SCAN_ATOMIC), ("-lb", npb.NP_SCAN_LOOKBACK)]
                  if gran in (npb.NP_GRAN_MULTIBLOCK, npb.NP_GRAN_GRID_DEVICE, npb.NP_GRAN_GRID_HOST) else [("", npb.NP_SCAN_ATOMIC)])

@@ -90,6 +90,29 @@ EXTRA = [
     ("persistent-grid1", dict(driver=npb.NP_DRIVER_PERSISTENT, parent_grid=1)),
     ("persistent-grid3-T1", dict(driver=npb.NP_DRIVER_PERSISTENT, parent_grid=3, threshold=1)),
     ("persistent-grid8-nodp", dict(variant=npb.NP_VARIANT_NODP, driver=npb.NP_DRIVER_PERSISTENT, parent_grid=8)),
+    # children below the threshold packed into the child grid: CTA shapes, drivers, scans
+    ("pack-pb64", dict(serial=npb.NP_SERIAL_PACKED, parent_block=64, threshold=8)),
+    ("pack-pb512-cb32", dict(serial=npb.NP_SERIAL_PACKED, parent_block=512, child_block=32, threshold=64)),
+    ("pack-cb1024", dict(serial=npb.NP_SERIAL_PACKED, child_block=1024, cfactor=1, threshold=16)),
+    ("pack-cb512-lb", dict(serial=npb.NP_SERIAL_PACKED, child_block=512, scan=npb.NP_SCAN_LOOKBACK, threshold=256)),
+    ("pack-grid1", dict(serial=npb.NP_SERIAL_PACKED, parent_grid=1, threshold=32)),
+    ("pack-grid3-lb", dict(serial=npb.NP_SERIAL_PACKED, parent_grid=3, scan=npb.NP_SCAN_LOOKBACK, threshold=128)),
+    ("pack-T1024-C16", dict(serial=npb.NP_SERIAL_PACKED, threshold=1024, cfactor=16)),
+    ("pack-T1025", dict(serial=npb.NP_SERIAL_PACKED, threshold=1025)),
+    ("pack-driver-host", dict(serial=npb.NP_SERIAL_PACKED, driver=npb.NP_DRIVER_HOST, threshold=32)),
+    ("pack-driver-chunk3", dict(serial=npb.NP_SERIAL_PACKED, driver=npb.NP_DRIVER_CHUNK, unroll=3, threshold=32)),
+    ("pack-driver-while1", dict(serial=npb.NP_SERIAL_PACKED, driver=npb.NP_DRIVER_WHILE, unroll=1, threshold=64)),
+    # children below the threshold spread over the parent CTA
+    ("block-pb64", dict(serial=npb.NP_SERIAL_BLOCK, parent_block=64, threshold=8)),
+    ("block-pb512", dict(serial=npb.NP_SERIAL_BLOCK, parent_block=512, threshold=64)),
+    ("block-pb96-lb", dict(serial=npb.NP_SERIAL_BLOCK, parent_block=96, scan=npb.NP_SCAN_LOOKBACK, threshold=4)),
+    ("block-grid1", dict(serial=npb.NP_SERIAL_BLOCK, parent_grid=1, threshold=32)),
+    ("block-grid3-lb", dict(serial=npb.NP_SERIAL_BLOCK, parent_grid=3, scan=npb.NP_SCAN_LOOKBACK, threshold=128)),
+    ("block-never", dict(serial=npb.NP_SERIAL_BLOCK, threshold=npb.INT32_MAX)),
+    ("block-driver-host", dict(serial=npb.NP_SERIAL_BLOCK, driver=npb.NP_DRIVER_HOST, threshold=32)),
+    ("block-driver-while1", dict(serial=npb.NP_SERIAL_BLOCK, driver=npb.NP_DRIVER_WHILE, unroll=1)),
+    ("spread-driver-while", dict(serial=npb.NP_SERIAL_SPREAD, driver=npb.NP_DRIVER_WHILE, threshold=32)),
+    ("spread-grid3", dict(serial=npb.NP_SERIAL_SPREAD, parent_grid=3, threshold=16)),
 ]
 
 
@@ -203,7 +226,14 @@ BT_FORMS = [("nodp", {}), ("cdp", {}), ("t", {}), ("tc", {}), ("tca", {}),
             ("tca", dict(granularity="multiblock", group_blocks=4, cfactor=2)),
             ("tca", dict(granularity="grid_device", scan=npb.NP_SCAN_ATOMIC)),
             ("tca", dict(granularity="grid_host", threshold=0, cfactor=16, child_block=64)),
-            ("tca", dict(threshold=npb.INT32_MAX))]
+            ("tca", dict(threshold=npb.INT32_MAX)),
+            ("tca", dict(serial=npb.NP_SERIAL_SPREAD)),
+            ("tca", dict(serial=npb.NP_SERIAL_PACKED, threshold=1024, scan=npb.NP_SCAN_LOOKBACK, parent_block=512,
+                         child_block=32)),
+            ("tca", dict(serial=npb.NP_SERIAL_PACKED, threshold=200, child_block=1024, cfactor=1)),
+            ("tca", dict(serial=npb.NP_SERIAL_BLOCK, threshold=64)),
+            ("tca", dict(serial=npb.NP_SERIAL_BLOCK, threshold=npb.INT32_MAX, parent_block=64,
+                         scan=npb.NP_SCAN_LOOKBACK))]
 
 
 @pytest.mark.parametrize("form,kw", BT_FORMS, ids=[f"{f}-{i}" for i, (f, _) in enumerate(BT_FORMS)])
@@ -373,11 +403,15 @@ def rmat20():
     return g, DevGraph(g)
 
 
-@pytest.mark.parametrize("form", ["tca", "nodp", "tca-mb", "tca-atomic", "tca-persistent", "nodp-persistent"])
+@pytest.mark.parametrize("form", ["tca", "nodp", "tca-mb", "tca-atomic", "tca-persistent", "nodp-persistent",
+                                  "tca-block", "tca-packed", "tca-block-lookback"])
 def test_rmat20_sssp_bfs_full(ctx, rmat20, form):
     g, dg = rmat20
     kw = {"tca-mb": dict(granularity="multiblock", group_blocks=8),
           "tca-atomic": dict(scan=npb.NP_SCAN_ATOMIC),
+          "tca-block": dict(serial=npb.NP_SERIAL_BLOCK),
+          "tca-packed": dict(serial=npb.NP_SERIAL_PACKED),
+          "tca-block-lookback": dict(serial=npb.NP_SERIAL_BLOCK, scan=npb.NP_SCAN_LOOKBACK, threshold=256),
           "tca-persistent": dict(driver=npb.NP_DRIVER_PERSISTENT),
           "nodp-persistent": dict(driver=npb.NP_DRIVER_PERSISTENT)}.get(form, {})
     cfg = npb.config(form.split("-")[0], **kw)
