@@ -85,10 +85,9 @@ WORKLOADS = {
 # per-workload values of the aggregated form's knobs, from threshold x cfactor x child-block
 # sweeps on GB300 (the paper also tunes T and CF per benchmark); other workloads use the defaults
 TUNED = {# tessellation: 512-thread parent CTAs make the output-offset look-back groups 16 tiles long
-         "bt64k": dict(parent_block=512, child_block=32, cfactor=4), "tc-rmat17": dict(threshold=8, child_block=32, cfactor=1),
-         # the 4096-vertex graph is latency-bound: the persistent level loop on 8 CTAs keeps its
-         # per-level grid barriers cheap (124 us against 141 us with the graph driver)
-         "bfs4k": dict(driver=4, parent_grid=8)}   # driver 4: NP_DRIVER_PERSISTENT
+         "bt64k": dict(parent_block=512, child_block=32, cfactor=4), "tc-rmat17": dict(threshold=8, child_block=32, cfactor=1)}
+# (the 4096-vertex graph, latency-bound, runs almost every level in the while driver's one-CTA
+# small-level loop: 115 us, against 150 us on the persistent level loop with 8 CTAs)
 
 
 def log(*a):
@@ -624,9 +623,9 @@ def run_ours(args, ws, rank, local):
             torch.distributed.destroy_process_group()
         return
 
-    # kernels launched per solve: graph solves launch init + per while-body
-    # iteration `unroll` x (parent, child) + the condition kernel; a
-    # tessellation launches init, parent and child
+    # kernels launched per solve: graph solves launch init (+ the small-level loop once before
+    # the while loop) + per while-body iteration `unroll` x (parent, child) + the condition
+    # kernel (the small-level loop); a tessellation launches init, parent and child
     if wl["kind"] == "bezier":
         per_solve = 3
     elif wl["kind"] == "tc":
@@ -635,7 +634,8 @@ def run_ours(args, ws, rank, local):
         # init + while-body iterations x (unroll x (parent, child) + condition) (+ the SSSP
         # distances written from the packed state)
         loop = 1 if cfg.driver == npb.NP_DRIVER_PERSISTENT else st["graph_iterations"] * (2 * cfg.unroll + 1)
-        per_solve = 1 + loop + (1 if wl["kind"] == "sssp" else 0)
+        pre = 1 if cfg.driver != npb.NP_DRIVER_PERSISTENT and cfg.small_parents > 0 else 0
+        per_solve = 1 + pre + loop + (1 if wl["kind"] == "sssp" else 0)
     gpu_launches = int(per_solve * args.steps)
     metric = METRIC if args.workload == "sssp-rmat20" else \
         f"{W.unit} and ms/solve ({args.workload}): aggregated form vs plain CDP; % HBM roofline"
@@ -1001,7 +1001,8 @@ def run_batched(args, ws, rank, local, wl):
     step_bytes = kb["solve"]
     groups = sum(c["groups"] for c in classes)
     per_iter = 2 * 4 + 1
-    gpu_launches = int(args.steps * (2 * groups + st["graph_iterations"] * per_iter))
+    # per group: fill, seed, the small-level loop before the while loop (on by default)
+    gpu_launches = int(args.steps * (3 * groups + st["graph_iterations"] * per_iter))
     line = {"metric": f"GTEPS and ms/batch ({args.workload}): 512 instances in one graph launch, autotuned per "
                       f"size class", "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

@@ -108,6 +108,8 @@ typedef int32_t np_status;
  *                     them ({parent, start, N, first item}), and each child
  *                     CTA takes chunks of 1024 items, stages the chunk's
  *                     records in shared memory and searches there. */
+#define NP_SMALL_PARENTS_MAX 1024
+
 #define NP_SERIAL_SPREAD 0
 #define NP_SERIAL_PACKED 1
 #define NP_SERIAL_BLOCK 2
@@ -128,7 +130,11 @@ typedef struct np_config {
   int32_t unroll;        /* levels per graph chunk or per while-body, 1..16 */
   int32_t parent_grid;   /* persistent parent CTAs; 0 = resident capacity */
   int32_t serial;        /* NP_SERIAL_*: where the children of parents below the threshold run */
-  int32_t reserved[3];   /* must be zero */
+  int32_t small_parents; /* grid-host form, while driver: at the start of each while-body
+                            iteration one CTA runs whole levels itself while the frontier
+                            has at most this many parents (<= NP_SMALL_PARENTS_MAX) and at
+                            most 16384 children in all; 0 = off */
+  int32_t reserved[2];   /* must be zero */
 } np_config;
 
 /* Fills the library defaults: CDP, threshold 32, cfactor 4, grid-host

@@ -307,6 +307,7 @@ np_status np_config_default(np_config* cfg) {
   cfg->unroll = 4;
   cfg->parent_grid = 0;
   cfg->serial = NP_SERIAL_SPREAD;
+  cfg->small_parents = NP_SMALL_PARENTS_MAX;
   return NP_OK;
 }
 

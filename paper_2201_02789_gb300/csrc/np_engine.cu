@@ -349,7 +349,8 @@ np_status check_config(const np_config* cfg) {
   if (cfg->parent_grid < 0) return NP_ERR_INVALID;
   if (cfg->serial != NP_SERIAL_SPREAD && cfg->serial != NP_SERIAL_PACKED && cfg->serial != NP_SERIAL_BLOCK)
     return NP_ERR_INVALID;
-  for (int k = 0; k < 3; k++)
+  if (cfg->small_parents < 0 || cfg->small_parents > NP_SMALL_PARENTS_MAX) return NP_ERR_INVALID;
+  for (int k = 0; k < 2; k++)
     if (cfg->reserved[k] != 0) return NP_ERR_INVALID;
   return NP_OK;
 }
@@ -383,6 +384,7 @@ Plan make_plan(const BodyKernels& K, const np_config& cfg) {
     p.parent = form == NP_SERIAL_SPREAD ? K.parent_grid_host : K.parent_cta;
     p.child = form == NP_SERIAL_PACKED ? K.child_agg_pack[cfi] : K.child_agg[cfi];
     p.loop = K.level_loop_agg[cfi];
+    p.small = cfg.small_parents > 0 ? K.level_small : nullptr;
     p.mode = M_GRID_HOST;
     p.gran = G_GRID_HOST;
   } else {
@@ -423,6 +425,7 @@ void base_args(const Workspace& w, const np_config& cfg, Args& a) {
   a.agg_threshold = (cfg.granularity == NP_GRAN_WARP || cfg.granularity == NP_GRAN_BLOCK) ? cfg.agg_threshold : 0;
   a.scan = cfg.scan;
   a.pack = serial_form(cfg) == NP_SERIAL_PACKED ? 1 : 0;
+  a.small_parents = cfg.small_parents;
   a.prec = wsp<int4>(w, w.lay.off_prec);
   a.pfirst = wsp<int>(w, w.lay.off_pfirst);
   a.b.st = w.st;
@@ -634,6 +637,22 @@ np_status add_while_node(Engine& e, LevelState* st, cudaGraph_t graph, const cud
                          const Plan& p, const Args& a, const Grids& g, int K, cudaGraphNode_t* node) {
   cudaGraphConditionalHandle h;
   NP_CK(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+  // With the small-level loop: one run of it before the loop, which sets the
+  // loop's condition itself (a traversal that stays small never enters it).
+  cudaGraphNode_t pre;
+  if (p.small) {
+    Args sa = a;
+    int k0 = 0, in_body = 0;
+    void* sargs[] = {&sa, &h, &k0, &in_body};
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void*>(p.small);
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1024);
+    kp.kernelParams = sargs;
+    NP_CK(cudaGraphAddKernelNode(&pre, graph, deps, ndeps, &kp));
+    deps = &pre;
+    ndeps = 1;
+  }
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = h;
@@ -644,8 +663,18 @@ np_status add_while_node(Engine& e, LevelState* st, cudaGraph_t graph, const cud
   NP_CK(cudaStreamBeginCaptureToGraph(e.cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   np_status s = NP_OK;
   for (int k = 0; k < K && s == NP_OK; k++) s = enqueue_pass(p, a, g, true, k, e.cap_stream);
-  void* cargs[] = {&st, &h, &K};
-  cudaError_t le = launch_pdl((const void*)set_cond_kernel, dim3(1), dim3(1), cargs, e.cap_stream, kPdl);
+  // end of the body: the small-level loop, or a one-thread kernel, moves the
+  // base on and sets the condition
+  cudaError_t le;
+  if (p.small) {
+    Args sa = a;
+    int in_body = 1;
+    void* sargs[] = {&sa, &h, &K, &in_body};
+    le = launch_pdl(p.small, dim3(1), dim3(1024), sargs, e.cap_stream, kPdl);
+  } else {
+    void* cargs[] = {&st, &h, &K};
+    le = launch_pdl((const void*)set_cond_kernel, dim3(1), dim3(1), cargs, e.cap_stream, kPdl);
+  }
   cudaError_t ce = cudaStreamEndCapture(e.cap_stream, &body);
   if (s != NP_OK) return s;
   NP_CK(le);

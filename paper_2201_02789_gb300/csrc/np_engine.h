@@ -51,6 +51,7 @@ struct Plan {
   const void* parent = nullptr;
   const void* child = nullptr;  // persistent child grid (grid-host form)
   const void* loop = nullptr;   // persistent level loop (NODP and grid-host forms)
+  const void* small = nullptr;  // one-CTA small-level loop at the start of each while body (grid-host)
   int mode = M_NODP;
   int gran = G_NODP;
 };

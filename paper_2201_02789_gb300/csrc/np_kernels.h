@@ -26,6 +26,7 @@ struct BodyKernels {
   const void* level_loop_agg[kNumCF];         // level_loop<Body, 1, cf>: persistent grid-aggregation loop
   const void* parent_cta;                     // parent_cta<Body>: grid-host, CTA tiles (serial modes BLOCK, PACKED)
   const void* child_agg_pack[kNumCF];         // child_agg_pack<Body, cf>: the child grid of PACKED
+  const void* level_small;                    // level_small<Body>: one-CTA loop over small levels (or NULL)
 };
 
 const BodyKernels& bfs_kernels();

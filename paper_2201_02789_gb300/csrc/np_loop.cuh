@@ -92,3 +92,131 @@ __global__ void __launch_bounds__(1024) level_loop(Args a, int max_levels) {
 }
 
 }  // namespace nestpar
+
+namespace nestpar {
+
+// ---------------------------------------------------------- small-level loop
+//
+// A level with few parents and few children costs mostly fixed latency: two
+// kernel boundaries and a dependent chain of L2 round trips in each grid.
+// Under the conditional-while driver of the grid-host form this one-CTA kernel
+// runs whole levels itself while the frontier holds at most a.small_parents
+// (<= blockDim.x) parents with at most kSmallItems children in all: each
+// thread takes one parent (count, row bounds), a CTA scan gives the items'
+// offsets, the parents are staged in shared memory, and the CTA's threads take
+// the items, each finding its parent by a binary search over the staged
+// offsets; CTA barriers separate the levels. It keeps the level state as the
+// parent and child grids do (slots and the count two levels ahead cleared,
+// counts rotated), so the grids continue from the level where it stops: the
+// first one too large, or an empty frontier. It runs once before the loop and
+// at the end of every body in place of the condition kernel: it moves the base
+// on by the body's K levels, runs what it can, and sets the loop's condition
+// (iterations counted and capped only at the end of a body).
+constexpr int kSmallItems = 16384;
+
+template <class Body>
+__global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditionalHandle h, int K, int in_body) {
+  NP_PDL_ENTRY();
+  constexpr int KS = 4;
+  __shared__ int s_first[1024];
+  __shared__ int4 s_rec[1024];
+  __shared__ uint2 s_scan[33];
+  __shared__ int s_stage[kCtaStage];
+  __shared__ int s_stage_n, s_stage_base;
+  LevelState* st = a.st;
+  const int tid = (int)threadIdx.x, nt = (int)blockDim.x;
+  const int limit = a.small_parents < nt ? a.small_parents : nt;
+  const int max_levels = __ldcg(&st->max_levels);
+  const int L0 = __ldcg(&st->base) + K;
+  int L = L0;
+  unsigned long long n_par = 0, n_items = 0, n_serial = 0;
+  for (;;) {
+    // written before this kernel or by this CTA before the last barrier: the
+    // same value in every thread
+    const int count = __ldcg(&st->count[L % 3]);
+    if (count <= 0 || count > limit || L >= max_levels) break;
+    const int* ids = (L & 1) ? a.fr1 : a.fr0;
+    int pid = 0, base = 0, N = 0;
+    if (tid < count) pid = __ldcg(&ids[tid]);
+    const bool valid = tid < count && pid >= 0;
+    if (valid) Body::count(a, pid, base, N);
+    unsigned e0, e1, items, t1;
+    block_scan2((unsigned)N, 0u, e0, e1, items, t1, s_scan);
+    if (items > (unsigned)kSmallItems) break;   // uniform: the grids take this level
+    if (tid == 0) {
+      level_open(st, L, count);
+      s_stage_n = 0;
+    }
+    BodyArgs b = a.b;
+    b.L = L;
+    b.next = (L & 1) ? a.fr0 : a.fr1;
+    b.next_count = &st->count[(L + 1) % 3];
+    if (tid < count) {
+      // parents without children keep a slot: the search takes the last parent
+      // whose first item is <= t, which is the one holding t
+      s_first[tid] = (int)e0;
+      s_rec[tid] = make_int4(pid, base, N, valid ? (int)Body::aux(b, pid) : 0);
+    }
+    __syncthreads();
+    StageSink sink{b.next, b.next_count, s_stage, &s_stage_n};
+    int top = 1;
+    while (top * 2 <= count) top *= 2;
+    for (int t0 = 0; t0 < (int)items; t0 += KS * nt) {
+      typename Body::F f[KS];
+      typename Body::P pk[KS];
+      bool v[KS];
+      int idx[KS];
+#pragma unroll
+      for (int k = 0; k < KS; k++) {
+        const int t = t0 + k * nt + tid;
+        v[k] = t < (int)items;
+        int r = 0;
+        for (int step = top; step > 0; step >>= 1)
+          if (r + step < count && s_first[r + step] <= t) r += step;
+        const int4 q = s_rec[r];
+        idx[k] = t - s_first[r];
+        pk[k] = Body::parent_aux(b, q.x, q.y, q.z, (unsigned)q.w);
+        f[k] = v[k] ? Body::fetch(b, pk[k], idx[k]) : typename Body::F{};
+      }
+      bool pf[KS];
+      int pv[KS];
+      Body::template apply_batch<KS>(b, pk, idx, f, v, pf, pv);
+      if constexpr (Body::kPushes) sink.template push<KS>(pf, pv);
+    }
+    // appends reach the next frontier and its count before the next level reads them
+    if constexpr (Body::kPushes) stage_flush(s_stage, &s_stage_n, b.next, b.next_count, &s_stage_base);
+    n_par += valid ? 1u : 0u;
+    n_items += (unsigned)N;
+    n_serial += N > 0 ? 1u : 0u;
+    __syncthreads();
+    L++;
+  }
+  if (L != L0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n_par += __shfl_xor_sync(kFull, n_par, o);
+      n_items += __shfl_xor_sync(kFull, n_items, o);
+      n_serial += __shfl_xor_sync(kFull, n_serial, o);
+    }
+    if ((tid & 31) == 0) {
+      add_stat(st, S_PARENTS, n_par);
+      add_stat(st, S_ITEMS, n_items);
+      add_stat(st, S_SERIAL, n_serial);
+    }
+  }
+  if (tid == 0) {
+    st->base = L;
+    bool more = __ldcg(&st->count[L % 3]) > 0 && L < max_levels;
+    if (in_body) {
+      // the iteration cap turns a level loop that failed to terminate into an error
+      const int it = ++st->body_iters;
+      if (more && it > max_levels + 16) {
+        st->error |= kErrTimeout;
+        more = false;
+      }
+    }
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+  }
+}
+
+}  // namespace nestpar

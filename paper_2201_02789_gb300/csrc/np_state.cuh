@@ -252,6 +252,8 @@ struct Args {
   // kPackItems items the record holding the chunk's first item
   int4* prec;
   int* pfirst;
+  int small_parents;             // > 0: the while body's one-CTA loop runs levels of at most this many parents
+  int pad2;
 };
 
 struct AggSeg {

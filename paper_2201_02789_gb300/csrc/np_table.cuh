@@ -46,6 +46,8 @@ inline BodyKernels make_table() {
   t.child_agg_pack[2] = (const void*)child_agg_pack<Body, 4>;
   t.child_agg_pack[3] = (const void*)child_agg_pack<Body, 8>;
   t.child_agg_pack[4] = (const void*)child_agg_pack<Body, 16>;
+  // level loops only: bodies that append to the next frontier
+  t.level_small = Body::kPushes ? (const void*)level_small<Body> : nullptr;
   return t;
 }
 

@@ -163,21 +163,51 @@ def _edge_graphs():
     out["dups"] = _graph_from_edges(6, [(0, 1), (0, 1), (1, 1), (1, 2), (2, 0), (2, 3), (3, 3), (3, 4), (0, 4)])
     out["road"] = gen.road_grid(60, 70, seed=6)
     out["rmat12"] = gen.rmat(12, 8, seed=13)
+    out["switch"] = _switch_graph()
     return out
+
+
+def _switch_graph():
+    """Levels that cross the one-CTA small-level loop's limits (1024 parents, 16384
+    children) in both directions, twice: a short path, a vertex with 20000 children,
+    a level of 20000 parents funnelling into 600, a path again, a fan-out of 30000,
+    and a path tail."""
+    rng = np.random.default_rng(77)
+    edges = [(0, 1), (1, 2)]
+    a0 = 3
+    edges += [(2, a0 + i) for i in range(20000)]               # 1 parent, 20000 children
+    b0 = a0 + 20000
+    edges += [(a0 + i, b0 + int(rng.integers(0, 600))) for i in range(20000)]   # 20000 parents
+    c0 = b0 + 600
+    edges += [(b0 + i, c0) for i in range(600)]                 # 600 parents, 600 children
+    edges += [(c0 + i, c0 + i + 1) for i in range(5)]           # path
+    d0 = c0 + 6
+    edges += [(c0 + 5, d0 + i) for i in range(30000)]           # 1 parent, 30000 children
+    e0 = d0 + 30000
+    edges += [(d0 + i, e0 + i % 40) for i in range(30000)]      # 30000 parents, 40 children each way
+    edges += [(e0 + i, e0 + 40) for i in range(40)]
+    edges += [(e0 + 40 + i, e0 + 41 + i) for i in range(8)]     # path tail
+    n = e0 + 49
+    ws = [int(x) for x in rng.integers(1, 256, size=len(edges))]
+    return _graph_from_edges(n, edges, ws)
 
 
 EDGE = _edge_graphs()
 
 
 @pytest.mark.parametrize("gname", list(EDGE))
-@pytest.mark.parametrize("form", ["nodp", "cdp", "tc", "tca", "mb", "block", "persist", "persist-nodp"])
+@pytest.mark.parametrize("form", ["nodp", "cdp", "tc", "tca", "mb", "block", "persist", "persist-nodp",
+                                  "tca-nosmall", "tca-small1", "tca-small33-cta"])
 def test_edge_graphs(ctx, gname, form):
     g = EDGE[gname]
     kw = {"mb": dict(granularity="multiblock", group_blocks=2, threshold=4),
+          "tca-nosmall": dict(small_parents=0),
+          "tca-small1": dict(small_parents=1, unroll=1),
+          "tca-small33-cta": dict(small_parents=33, serial=npb.NP_SERIAL_BLOCK, unroll=3),
           "block": dict(granularity="block", threshold=1, cfactor=2),
           "persist": dict(driver=npb.NP_DRIVER_PERSISTENT, threshold=2),
           "persist-nodp": dict(driver=npb.NP_DRIVER_PERSISTENT)}.get(form, {})
-    base = {"persist": "tca", "persist-nodp": "nodp"}.get(form, form)
+    base = {"persist": "tca", "persist-nodp": "nodp"}.get(form, form.split("-")[0])
     cfg = npb.config(base if base in ("nodp", "cdp", "tc", "tca") else "tca", **kw)
     dg = DevGraph(g)
     for src in sorted({0, g.n - 1, g.n // 2}):
@@ -441,8 +471,9 @@ def test_bt64k_full(ctx):
 
 def test_bench_tuned_configs_full(ctx, g4k):
     """The configurations bench.py times where they differ from the library default (BT-64K
-    with 32-thread child blocks and CF 8; the 4096-vertex BFS on the persistent loop with 8
-    CTAs), at full size, against the oracle."""
+    with 512-thread parent CTAs, 32-thread child blocks and CF 4; the triangle-counting
+    setting is checked in its own tests), and the 4096-vertex graph on the persistent loop
+    with 8 CTAs, which it used to time, at full size, against the oracle."""
     import bench
     cfg = npb.config("tca", **bench.TUNED["bt64k"])
     ctrl = gen.bt64k()
@@ -453,7 +484,7 @@ def test_bench_tuned_configs_full(ctx, g4k):
     ok, worst = bezier_tolerance_ok(pts, ref_pts)
     assert ok, worst
     g, dg, ref_l, ref_d = g4k
-    cfg = npb.config("tca", **bench.TUNED["bfs4k"])
+    cfg = npb.config("tca", driver=npb.NP_DRIVER_PERSISTENT, parent_grid=8)
     lv, st = bfs(ctx, dg, 0, cfg, stats=True)
     np.testing.assert_array_equal(lv, ref_l)
     d, st2 = sssp(ctx, dg, 0, cfg, stats=True)
