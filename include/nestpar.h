@@ -257,6 +257,14 @@ typedef struct np_batch_class {
   double tuned_ms;            /* the class's time under `config` when tuned (0 = not tuned) */
   int32_t candidates;         /* configurations the tuner timed */
   int32_t reserved2;
+  /* The tuner's device-launch candidates (granularity block, multi-block of 8
+   * parent blocks or grid-device, threshold 32 or 512, cfactor 4), timed on the
+   * class as stream-ordered launches outside the batch graph: a graph kernel
+   * node does not wait for the grids it launches from the device, so these
+   * forms cannot run inside the one-launch batch. The fastest of them: */
+  double device_launch_ms;    /* its time (0 = not measured) */
+  int32_t device_launch_granularity;   /* its NP_GRAN_* */
+  int32_t device_launch_threshold;     /* its threshold */
 } np_batch_class;
 
 typedef struct np_batch np_batch;
@@ -269,11 +277,13 @@ np_status np_batch_destroy(np_batch *b);
 np_status np_batch_layout(const np_batch *b, int64_t *offsets, int64_t *total);
 np_status np_batch_classes(const np_batch *b, np_batch_class *out, int32_t max, int32_t *nclasses);
 np_status np_batch_set_config(np_batch *b, int32_t cls, const np_config *cfg);
-/* Autotuner. For each class, runs the class's groups alone under each
- * candidate configuration (no dynamic parallelism; grid-host aggregation with
- * threshold T in {8, 32, 128, 512}, coarsening factor in {2, 8} and child
- * block in {32, 128}), `reps` times each (0 = 3), and keeps the configuration
- * with the least minimum time. `out` (device, total elements) is overwritten. */
+/* Autotuner (Section VII-C tunes threshold, coarsening and granularity). For
+ * each class, runs the class's groups alone under each candidate configuration
+ * (no dynamic parallelism; grid-host aggregation with threshold T in {8, 32,
+ * 128, 512}, coarsening factor in {2, 8} and child block in {32, 128}), `reps`
+ * times each (0 = 3), and keeps the configuration with the least minimum time.
+ * It also times the device-launch granularities (see np_batch_class), which
+ * it reports but cannot pick. `out` (device, total elements) is overwritten. */
 np_status np_batch_tune(np_batch *b, void *out, int32_t reps, void *stream);
 /* Solves every instance into `out` (device int32 levels or uint32 distances,
  * total elements). stats (nullable, waits) are summed over groups. */
@@ -362,30 +372,35 @@ np_status np_triangles(np_ctx *ctx, const np_csr *dag, uint64_t *count, const np
 
 /* ---- allocation-free tessellation (the paper has no counterpart) ----
  * Some callers cannot allocate device memory at the time they call this
- * library: code recording its GPU work into a CUDA graph by stream capture
- * (an allocation is not a capturable operation), programs whose device
- * memory all belongs to their own pool allocator or to a budget fixed at
- * start-up, and latency-critical loops where an allocation may wait for the
- * device. np_bezier_noalloc serves them: the same tessellation as np_bezier
- * (same kernels, same results), with no context and no allocation of any
- * kind. Its scratch (level state, aggregation records, look-back tile states)
- * is one static device array of about 1.5 MB inside the library, sized for
+ * library: programs whose device memory all belongs to their own pool
+ * allocator or to a budget fixed at start-up, and latency-critical loops where
+ * an allocation may wait for the device. np_bezier_noalloc serves them: the
+ * same tessellation as np_bezier (the kernels np_bezier runs for `cfg`, the
+ * same results), with no context and no allocation of any kind. Its scratch
+ * (level state, aggregation records, look-back tile states) is one static
+ * device array of about 1.5 MB inside the library, sized for
  * NP_NOALLOC_MAX_CURVES curves; every GPU that loads the library holds it
  * until the process exits.
  *   - ncurves > NP_NOALLOC_MAX_CURVES is rejected with NP_ERR_INVALID before
- *     anything is enqueued; so are the argument errors of np_bezier.
+ *     anything is enqueued; so are the argument errors of np_bezier
+ *     (np_config checks included).
  *   - Only forms without device-side launches run here: NP_VARIANT_NODP, or
- *     NP_VARIANT_CDP with NP_GRAN_GRID_HOST; other forms get NP_ERR_UNSUPPORTED.
+ *     NP_VARIANT_CDP with NP_GRAN_GRID_HOST and serial children in the parent
+ *     kernel (NP_SERIAL_SPREAD or NP_SERIAL_BLOCK); other forms get
+ *     NP_ERR_UNSUPPORTED.
  *   - The first call on a device looks up the array's device address and
  *     clears the array with an asynchronous memset on `stream`; make that
- *     first call before any stream capture.
+ *     first call before any stream capture. The address is kept for the life
+ *     of the process: after cudaDeviceReset the entry point must not be used.
  *   - All calls share the array, which keeps the last call's contents; each
  *     call resets what must start at zero. Calls that overlap on the GPU (on
  *     different streams, or from several host threads) race on the array and
  *     must be serialised by the caller.
- *   - The call only enqueues work on `stream`; it reports no device-side
- *     status and no stats. A capacity shortfall shows as
- *     offsets[ncurves] > cap (curves that do not fit are skipped). */
+ *   - The call only enqueues work on `stream`; it returns no stats. Its
+ *     outcome is in offsets[ncurves] once the stream reaches it: the total
+ *     point count; > cap when the capacity falls short (curves that do not fit
+ *     are skipped); -1 when a bounded device-side wait gave up (the offsets
+ *     are then not to be used). */
 #define NP_NOALLOC_MAX_CURVES 65536
 np_status np_bezier_noalloc(const float *ctrl, int32_t ncurves, int32_t *offsets, float *points,
                             int64_t cap, const np_config *cfg, void *stream);

@@ -59,6 +59,8 @@ struct Class {
   np_config cfg{};
   double tuned_ms = 0.0;
   int candidates = 0;
+  double dl_ms = 0.0;            // the fastest device-launch candidate (reported, not picked)
+  int dl_gran = 0, dl_threshold = 0;
   int instances = 0;
   int64_t vertices = 0, edges = 0;
 };
@@ -239,7 +241,11 @@ np_status batch_stats(np_batch* b, cudaStream_t s, np_stats* stats) {
 }
 
 // Runs the groups of class `ci` alone under cfg, reps times; min time in ms.
-np_status time_class(np_batch* b, int ci, const np_config& cfg, void* out, int reps, cudaStream_t s, double* ms) {
+// Device-launch forms run as stream-ordered launches (host-replayed level
+// chunks); a launch the device refused ran serially and still gave the exact
+// result, so with tolerate_launch it does not fail the timing.
+np_status time_class(np_batch* b, int ci, const np_config& cfg, void* out, int reps, cudaStream_t s, double* ms,
+                     bool tolerate_launch = false) {
   Class& c = b->classes[(size_t)ci];
   Plan p = make_plan(kernels_of(b->kind), cfg);
   double best = 1e30;
@@ -261,7 +267,8 @@ np_status time_class(np_batch* b, int ci, const np_config& cfg, void* out, int r
   }
   for (int gi : c.groups) {
     np_stats one;
-    NP_TRY(finish(b->e, b->groups[(size_t)gi].ws, s, &one));
+    const np_status fs = finish(b->e, b->groups[(size_t)gi].ws, s, &one);
+    if (fs != NP_OK && !(tolerate_launch && fs == NP_ERR_LAUNCH)) return fs;
   }
   *ms = best;
   return NP_OK;
@@ -434,6 +441,9 @@ np_status np_batch_classes(const np_batch* b, np_batch_class* out, int32_t max, 
     r.config = c.cfg;
     r.tuned_ms = c.tuned_ms;
     r.candidates = c.candidates;
+    r.device_launch_ms = c.dl_ms;
+    r.device_launch_granularity = c.dl_gran;
+    r.device_launch_threshold = c.dl_threshold;
     out[i] = r;
   }
   return NP_OK;
@@ -491,6 +501,28 @@ np_status np_batch_tune(np_batch* b, void* out, int32_t reps, void* stream) {
     b->classes[ci].cfg = pick;
     b->classes[ci].tuned_ms = best;
     b->classes[ci].candidates = (int)cands.size();
+    // the device-launch granularities, for the record (Section VII-C's third axis)
+    double dl_best = 1e30;
+    for (int gran : {NP_GRAN_BLOCK, NP_GRAN_MULTIBLOCK, NP_GRAN_GRID_DEVICE})
+      for (int T : {32, 512}) {
+        np_config x = b->classes[ci].cfg;
+        x.variant = NP_VARIANT_CDP;
+        x.granularity = gran;
+        x.group_blocks = 8;
+        x.threshold = T;
+        x.cfactor = 4;
+        x.child_block = 64;
+        x.driver = NP_DRIVER_AUTO;
+        double ms = 0.0;
+        NP_TRY(time_class(b, (int)ci, x, out, 1, s, &ms, true));
+        NP_TRY(time_class(b, (int)ci, x, out, reps, s, &ms, true));
+        if (ms < dl_best) {
+          dl_best = ms;
+          b->classes[ci].dl_gran = gran;
+          b->classes[ci].dl_threshold = T;
+        }
+      }
+    b->classes[ci].dl_ms = dl_best;
   }
   drop_batch_graph(b);
   for (Group& g : b->groups) ws_drop_graphs(g.ws);

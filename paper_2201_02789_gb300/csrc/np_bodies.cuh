@@ -51,12 +51,7 @@ struct BfsBody {
     for (int k = 0; k < K; k++) {
       v[k] = f[k].v;
       cur[k] = 0;
-      if (valid[k]) {
-        if (NP_BFS_BITMAP && b.vbits)   // -1: not yet visited as far as this SM's copy of the bitmap knows
-          cur[k] = (NP_FILTER_LOAD(&b.vbits[(unsigned)v[k] >> 5]) >> (v[k] & 31)) & 1u ? 0 : -1;
-        else
-          cur[k] = NP_FILTER_LOAD(&b.level[v[k]]);
-      }
+      if (valid[k]) cur[k] = NP_FILTER_LOAD(&b.level[v[k]]);
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -64,11 +59,7 @@ struct BfsBody {
       if (push[k]) cur[k] = atomicCAS(&b.level[v[k]], -1, b.L + 1);
     }
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-      push[k] = push[k] && cur[k] == -1;
-      // the claim decides; the bit only lets later visits skip the CAS
-      if (NP_BFS_BITMAP && push[k] && b.vbits) atomicOr(&b.vbits[(unsigned)v[k] >> 5], 1u << (v[k] & 31));
-    }
+    for (int k = 0; k < K; k++) push[k] = push[k] && cur[k] == -1;
   }
 };
 
@@ -182,32 +173,14 @@ __device__ __forceinline__ unsigned intersect_merge4(const int* A, int na, const
   return c;
 }
 
-// Shared-memory hash set of a parent's out-list (the balanced child grid
-// builds one per child block, since a block's items all share one parent):
-// open addressing with linear probing, at most half full, -1 = empty.
-__device__ __forceinline__ unsigned tc_hash_slot(int x, int shift) {
-  return ((unsigned)x * 0x9E3779B1u) >> shift;
-}
-__device__ __forceinline__ bool tc_hash_contains(const int* tab, int shift, int x) {
-  const unsigned mask = 0xffffffffu >> shift;
-  for (unsigned h = tc_hash_slot(x, shift);; h = (h + 1) & mask) {
-    const int y = tab[h];
-    if (y == x) return true;
-    if (y < 0) return false;
-  }
-}
-
 struct TcBody {
   static constexpr bool kOffsets = false;
   static constexpr bool kPushes = false;
   static constexpr bool kBalance = true;    // block cost varies with the lists' lengths
   static constexpr int kStage = 0;
-  static constexpr int kHashSlots = 1024;   // per child block: parents with up to 512 out-edges
   struct P {
     int base;
     int n;
-    const int* hash;   // shared-memory hash set of this parent's list, or NULL
-    int shift;         // 32 - log2(table size)
   };
   struct F {
     int v;
@@ -216,33 +189,13 @@ struct TcBody {
     base = __ldg(&a.row_ptr[pid]);
     N = __ldg(&a.row_ptr[pid + 1]) - base;
   }
-  __device__ static P parent(const BodyArgs&, int, int base, int N) { return P{base, N, nullptr, 0}; }
+  __device__ static P parent(const BodyArgs&, int, int base, int N) { return P{base, N}; }
   __device__ static unsigned aux(const BodyArgs&, int) { return 0u; }
   __device__ static P parent_aux(const BodyArgs& b, int pid, int base, int N, unsigned) {
     return parent(b, pid, base, N);
   }
   __device__ static P shfl(const P& p, int src) {
-    return P{__shfl_sync(kFull, p.base, src), __shfl_sync(kFull, p.n, src), nullptr, 0};
-  }
-  // Builds the hash set of the parent's out-list in `tab` with the cb threads
-  // of one child block (tid in [0, cb)); `sync` joins those threads. Leaves p
-  // unchanged when the list does not fit.
-  template <class Sync>
-  __device__ static void build_block(const BodyArgs& b, P& p, int* tab, int tid, int cb, Sync sync) {
-    if (p.n > kHashSlots / 2) return;
-    int lg = 5;
-    while ((1 << lg) < 2 * p.n) lg++;
-    const int size = 1 << lg, shift = 32 - lg;
-    for (int t = tid; t < size; t += cb) tab[t] = -1;
-    sync();
-    for (int t = tid; t < p.n; t += cb) {
-      const int x = __ldg(&b.col[p.base + t]);
-      for (unsigned h = tc_hash_slot(x, shift);; h = (h + 1) & (unsigned)(size - 1))
-        if (atomicCAS(&tab[h], -1, x) == -1) break;   // list entries are distinct
-    }
-    sync();
-    p.hash = tab;
-    p.shift = shift;
+    return P{__shfl_sync(kFull, p.base, src), __shfl_sync(kFull, p.n, src)};
   }
   __device__ static F fetch(const BodyArgs& b, const P& p, int i) { return F{__ldg(&b.col[p.base + i])}; }
   template <int K>
@@ -265,18 +218,7 @@ struct TcBody {
       const int* walk = walk_u ? nu : nv;
       const int* look = walk_u ? nv : nu;
       const int nw = walk_u ? p[k].n : vn[k], nl = walk_u ? vn[k] : p[k].n;
-      if (NP_TC_HASH && p[k].hash && vn[k] <= 4 * p[k].n) {
-        // walk N+(v) with independent loads, probing the parent's hash set
-        int t = 0;
-        for (; t + 4 <= vn[k]; t += 4) {
-          int x[4];
-#pragma unroll
-          for (int q = 0; q < 4; q++) x[q] = __ldg(&nv[t + q]);
-#pragma unroll
-          for (int q = 0; q < 4; q++) c += tc_hash_contains(p[k].hash, p[k].shift, x[q]) ? 1u : 0u;
-        }
-        for (; t < vn[k]; t++) c += tc_hash_contains(p[k].hash, p[k].shift, __ldg(&nv[t])) ? 1u : 0u;
-      } else if (NP_TC_MERGE && nl <= 16 * nw) {
+      if (NP_TC_MERGE && nl <= 16 * nw) {
         c += intersect_merge4(walk, nw, look, nl);   // lists of comparable length
       } else {
         for (int t = 0; t < nw; t++) c += sorted_contains(look, nl, __ldg(&walk[t])) ? 1u : 0u;

@@ -22,8 +22,6 @@ struct np_ctx {
   unsigned long long* tri = nullptr;  // triangle-counting partial sums [kTcSlots]
   unsigned long long* dtag = nullptr; // packed SSSP state (dist << 32 | tag) of np_sssp / np_sssp_multi
   int64_t dtag_cap = 0;
-  unsigned* vbits = nullptr;          // visited bitmap of np_bfs (32 vertices per word)
-  int64_t vbits_cap = 0;
   // device staging for the *_host entry points
   unsigned char* stage = nullptr;
   size_t stage_bytes = 0;
@@ -47,18 +45,6 @@ np_status ensure_dtag(np_ctx* c, int64_t total) {
   return NP_OK;
 }
 
-np_status ensure_vbits(np_ctx* c, int64_t words) {
-  if (words <= c->vbits_cap) return NP_OK;
-  if (c->vbits) {
-    NP_CK(cudaDeviceSynchronize());
-    cudaFree(c->vbits);
-    c->vbits = nullptr;
-    c->vbits_cap = 0;
-  }
-  NP_CK(cudaMalloc(&c->vbits, sizeof(unsigned) * (size_t)words));
-  c->vbits_cap = words;
-  return NP_OK;
-}
 
 constexpr int kVersion = 10200;  // 1.2.0
 
@@ -92,17 +78,13 @@ np_status solve(np_ctx* c, int kind, const np_csr* g, int src, int* level, unsig
     a.b.dtag = c->dtag;
     // the caller's distance array holds the filter copy until the result overwrites it
     if (NP_SSSP_MIRROR) a.b.dmirror = dist;
-  } else if (NP_BFS_BITMAP) {
-    NP_TRY(ensure_vbits(c, ((int64_t)g->n + 31) / 32));
-    a.b.vbits = c->vbits;
   }
   const int blocks = (int)((g->n + 255) / 256 < 4096 ? (g->n + 255) / 256 : 4096);
   if (c->e.profile) NP_CK(cudaEventRecord(c->e.ev[0], s));
   if (kind == 1)
     init_dtag_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, g->n, src, c->dtag, a.fr0, g->n + 2, a.b.dmirror);
   else
-    init_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, kind, g->n, src, level, dist, a.b.stamp, a.fr0, g->n + 2,
-                                             a.b.vbits);
+    init_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, kind, g->n, src, level, dist, a.b.stamp, a.fr0, g->n + 2);
   NP_CK(cudaGetLastError());
   if (c->e.profile) {
     NP_CK(cudaEventRecord(c->e.ev[3], s));
@@ -344,7 +326,6 @@ np_status np_destroy(np_ctx* c) {
   if (c->ids) cudaFree(c->ids);
   if (c->tri) cudaFree(c->tri);
   if (c->dtag) cudaFree(c->dtag);
-  if (c->vbits) cudaFree(c->vbits);
   engine_release(c->e);
   delete c;
   return NP_OK;

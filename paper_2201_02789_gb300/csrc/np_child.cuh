@@ -87,14 +87,6 @@ __device__ __forceinline__ void child_agg_balanced(const BodyArgs& b, const int4
   int j = -1, next_off = 0, off = 0, N = 0, done = 0;
   typename Body::P p{};
   WarpSink sink{b.next, b.next_count};
-  // one hash table per child block (per_cta <= 8: CTAs of 256 threads, cb >= 32)
-  __shared__ int s_tab[NP_TC_HASH ? 8 * Body::kHashSlots : 1];
-  auto sub_sync = [&]() {
-    if (cb == 32)
-      __syncwarp();
-    else
-      asm volatile("bar.sync %0, %1;" ::"r"(1 + local), "r"(cb) : "memory");
-  };
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) *s_next = atomicAdd(ticket, per_cta);
@@ -110,9 +102,6 @@ __device__ __forceinline__ void child_agg_balanced(const BodyArgs& b, const int4
         next_off = j + 1 < nrec ? __ldcg(&boff[j + 1]) : 0x7fffffff;
         N = r.z;
         p = Body::parent(b, r.x, r.y, r.z);
-        if constexpr (NP_TC_HASH) {
-          if (per_cta <= 8) Body::build_block(b, p, s_tab + local * Body::kHashSlots, stid, cb, sub_sync);
-        }
       }
       run_coarsened<Body, CF>(b, p, N, B0 - off, cb, stid, sink);
       done++;
@@ -309,65 +298,6 @@ __device__ __forceinline__ void child_agg_staged(const BodyArgs& b, const int4* 
   if (stid == 0) mbar_inval(bar);
 }
 
-// One coarsened block of 4 original blocks (cb threads, 4·cb edges of one
-// parent) with 16-byte edge-list loads: thread t reads edges [a0 + 4t, a0 + 4t + 4)
-// of the block's window, a0 = the block's first edge rounded down to a multiple
-// of 4, with one int4 load per array when all four lie before the block's end
-// (edges before the block's start are read and ignored; they belong to the
-// list before it). A vector that straddles the end, and the up to three edges
-// past a0 + 4·cb, are read one by one, so no load leaves [a0, end of block).
-// Requires col (and w) 16-byte aligned.
-template <class Body, class Sink>
-__device__ __forceinline__ void run_coarsened_vec4(const BodyArgs& b, const typename Body::P& p, int base, int N,
-                                                   int bl, int cb, int tid, Sink& sink) {
-  constexpr bool kW = Body::kStage == 2;
-  const int span = 4 * cb;
-  const int e0 = base + bl * span;
-  const int e1 = min(base + N, e0 + span);
-  const int a0 = e0 & ~3;
-  const int ea = a0 + 4 * tid;
-  typename Body::F f[5];
-  bool v[5];
-  int idx[5];
-  int c[4] = {0, 0, 0, 0};
-  unsigned w[4] = {0u, 0u, 0u, 0u};
-  if (ea + 4 <= e1) {
-    const int4 c4 = __ldg(reinterpret_cast<const int4*>(b.col + ea));
-    c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
-    if constexpr (kW) {
-      const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(b.w + ea));
-      w[0] = w4.x; w[1] = w4.y; w[2] = w4.z; w[3] = w4.w;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      if (ea + q >= e0 && ea + q < e1) {
-        c[q] = __ldg(&b.col[ea + q]);
-        if constexpr (kW) w[q] = __ldg(&b.w[ea + q]);
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    const int e = ea + q;
-    v[q] = e >= e0 && e < e1;
-    idx[q] = e - base;
-    f[q] = v[q] ? Body::fetch_from(p, c[q], w[q]) : typename Body::F{};
-  }
-  // the block's last edges past the aligned window
-  const int et = a0 + span + tid;
-  v[4] = tid < 3 && et < e1;
-  idx[4] = et - base;
-  f[4] = v[4] ? Body::fetch_from(p, __ldg(&b.col[et]), kW ? __ldg(&b.w[et]) : 0u) : typename Body::F{};
-  bool pf[5];
-  int pv[5];
-  typename Body::P pk[5];
-#pragma unroll
-  for (int k = 0; k < 5; k++) pk[k] = p;
-  Body::template apply_batch<5>(b, pk, idx, f, v, pf, pv);
-  if constexpr (Body::kPushes) sink.template push<5>(pf, pv);
-}
-
 // Aggregated child blocks [0, total) of the records rec[0, nrec) with block
 // offsets boff: disaggregation + coarsened body. A CTA hosts blockDim.x / cb
 // child blocks of cb threads that run independently (no CTA barrier on this
@@ -405,10 +335,6 @@ __device__ __forceinline__ void child_agg_run(const BodyArgs& b, const int4* rec
   typename Body::P p{};
   __syncthreads();
   StageSink sink{b.next, b.next_count, s_stage, s_stage_n};
-  bool vec4 = false;
-  if constexpr (NP_VEC4 && CF == 4 && Body::kStage > 0)
-    vec4 = ((reinterpret_cast<unsigned long long>(b.col) |
-             (Body::kStage == 2 ? reinterpret_cast<unsigned long long>(b.w) : 0ull)) & 15ull) == 0ull;
   for (int B0 = first; B0 < last; B0++) {
     if (j < 0 || B0 >= next_off) {
       int4 r;
@@ -430,12 +356,6 @@ __device__ __forceinline__ void child_agg_run(const BodyArgs& b, const int4* rec
       p = Body::parent(b, r.x, r.y, r.z);
       if (j + 1 < nrec) rn = __ldcg(&rec[j + 1]);
       next2 = j + 2 < nrec ? __ldcg(&boff[j + 2]) : 0x7fffffff;
-    }
-    if constexpr (NP_VEC4 && CF == 4 && Body::kStage > 0) {
-      if (vec4) {
-        run_coarsened_vec4<Body>(b, p, base, N, B0 - off, cb, stid, sink);
-        continue;
-      }
     }
     run_coarsened<Body, CF>(b, p, N, B0 - off, cb, stid, sink);
   }

@@ -55,7 +55,7 @@ __device__ __forceinline__ void reset_slots(LevelState* st) {
 }
 
 __global__ void init_solve_kernel(LevelState* st, int kind, int n, int src, int* level, unsigned* dist,
-                                  int* stamp, int* fr0, int max_levels, unsigned* vbits) {
+                                  int* stamp, int* fr0, int max_levels) {
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     if (kind == 0) {
       level[v] = v == src ? 0 : -1;
@@ -63,11 +63,6 @@ __global__ void init_solve_kernel(LevelState* st, int kind, int n, int src, int*
       dist[v] = v == src ? 0u : 0xffffffffu;
       stamp[v] = -1;
     }
-  }
-  if (vbits) {
-    const int words = (n + 31) >> 5;
-    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < words; w += gridDim.x * blockDim.x)
-      vbits[w] = w == (src >> 5) ? 1u << (src & 31) : 0u;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     fr0[0] = src;

@@ -153,9 +153,8 @@ np_status launch_level_loop(Engine& e, const Plan& p, const Args& a, const np_co
                             cudaStream_t s);
 
 // ---- device-side initialisation kernels (np_engine.cu)
-// vbits (nullable): the BFS visited bitmap, cleared but for the source's bit.
 __global__ void init_solve_kernel(LevelState* st, int kind, int n, int src, int* level, unsigned* dist, int* stamp,
-                                  int* fr0, int max_levels, unsigned* vbits);
+                                  int* fr0, int max_levels);
 __global__ void init_fixed_kernel(LevelState* st);
 // Multi-source start: every element of level/dist/stamp[0, total) to its unreached value.
 __global__ void fill_unreached_kernel(int kind, long long total, int* level, unsigned* dist, int* stamp);

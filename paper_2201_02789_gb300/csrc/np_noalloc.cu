@@ -13,8 +13,7 @@
 #include <mutex>
 
 #include "nestpar.h"
-#include "np_device.cuh"
-#include "np_kernels.h"
+#include "np_engine.h"
 
 using namespace nestpar;
 
@@ -86,24 +85,26 @@ np_status device_scratch(cudaStream_t s, DeviceScratch* out) {
   return NP_OK;
 }
 
-bool valid_blocks(const np_config* c) {
-  return c->child_block >= 32 && c->child_block <= 1024 && c->child_block % 32 == 0 &&
-         c->parent_block >= 64 && c->parent_block <= kMaxParentBlock && c->parent_block % 32 == 0;
+// After the call's kernels: a bounded wait that gave up (look-back timeout)
+// leaves offsets it could not finish, so the total becomes -1 for the caller
+// to see (a call that completed never writes a negative total).
+__global__ void noalloc_status_kernel(const LevelState* st, int* offsets, int ncurves) {
+  if (st->error & kErrTimeout) offsets[ncurves] = -1;
 }
 
 }  // namespace
 
 extern "C" np_status np_bezier_noalloc(const float* ctrl, int32_t ncurves, int32_t* offsets, float* points,
                                        int64_t cap, const np_config* cfg, void* stream) {
-  if ((ncurves > 0 && !ctrl) || !offsets || !cfg || ncurves < 0 || cap < 0 || (cap > 0 && !points))
+  if ((ncurves > 0 && !ctrl) || !offsets || ncurves < 0 || cap < 0 || (cap > 0 && !points))
     return NP_ERR_INVALID;
+  np_status cs = check_config(cfg);   // the argument checks of np_bezier
+  if (cs != NP_OK) return cs;
   if (ncurves > kMaxCurves) return NP_ERR_INVALID;   // beyond the static scratch
-  const int cfi = cf_index(cfg->cfactor);
-  if (cfi < 0 || !valid_blocks(cfg) || (cfg->scan != NP_SCAN_LOOKBACK && cfg->scan != NP_SCAN_ATOMIC))
-    return NP_ERR_INVALID;
   const bool nodp = cfg->variant == NP_VARIANT_NODP;
-  if (!nodp && cfg->variant != NP_VARIANT_CDP) return NP_ERR_INVALID;
-  if (!nodp && cfg->granularity != NP_GRAN_GRID_HOST) return NP_ERR_UNSUPPORTED;   // device launches
+  // device launches, and packed serial children (records beyond the static scratch), are not run here
+  if (!nodp && (cfg->granularity != NP_GRAN_GRID_HOST || serial_form(*cfg) == NP_SERIAL_PACKED))
+    return NP_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (ncurves == 0) return cudaMemsetAsync(offsets, 0, sizeof(int32_t), s) == cudaSuccess ? NP_OK : NP_ERR_CUDA;
 
@@ -139,8 +140,10 @@ extern "C" np_status np_bezier_noalloc(const float* ctrl, int32_t ncurves, int32
   a.b.ctrl = ctrl;
   a.b.points = reinterpret_cast<float2*>(points);
 
+  // the kernels np_bezier runs for this configuration
   const BodyKernels& K = bezier_kernels();
-  const void* parent = nodp ? K.parent_nodp : K.parent_grid_host;
+  const Plan plan = make_plan(K, *cfg);
+  const void* parent = plan.parent;
   const int pb = cfg->parent_block, cb = cfg->child_block;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, parent, pb, 0) != cudaSuccess || occ < 1) occ = 1;
@@ -162,12 +165,14 @@ extern "C" np_status np_bezier_noalloc(const float* ctrl, int32_t ncurves, int32
     const int cthreads = cb < 256 ? 256 : cb;
     BodyArgs b = a.b;
     int cocc = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cocc, K.child_agg[cfi], cthreads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cocc, plan.child, cthreads, 0) != cudaSuccess ||
         cocc < 1)
       cocc = 1;
     void* cargs[] = {&b, &seg};
-    if (cudaLaunchKernel(K.child_agg[cfi], dim3(cocc * d.sms), dim3(cthreads), cargs, 0, s) != cudaSuccess)
+    if (cudaLaunchKernel(plan.child, dim3(cocc * d.sms), dim3(cthreads), cargs, 0, s) != cudaSuccess)
       return NP_ERR_CUDA;
   }
+  noalloc_status_kernel<<<1, 1, 0, s>>>(state, offsets, ncurves);
+  if (cudaGetLastError() != cudaSuccess) return NP_ERR_CUDA;
   return NP_OK;
 }

@@ -43,28 +43,10 @@
 #ifndef NP_SPREAD_BATCH
 #define NP_SPREAD_BATCH 8
 #endif
-// np_bfs filters child visits on a visited bitmap instead of level[] (an
-// option: the bit set after each claim costs more than the smaller filter saves)
-#ifndef NP_BFS_BITMAP
-#define NP_BFS_BITMAP 0
-#endif
-// aggregated child blocks of 4 original blocks read edge lists with 16-byte
-// loads (an option: the scalar loads are already coalesced, 128 bytes per warp
-// instruction, and measured faster)
-#ifndef NP_VEC4
-#define NP_VEC4 0
-#endif
 // triangle counting: intersect lists of comparable length by a blocked merge
 // (else by binary searches of the longer list)
 #ifndef NP_TC_MERGE
 #define NP_TC_MERGE 1
-#endif
-// triangle counting in the balanced child grid: a child block hashes its
-// parent's out-list in shared memory and probes it from the other list (an
-// option: the per-block table builds and 32 KB of shared memory per CTA cost
-// more than the independent probes gain over the blocked merge)
-#ifndef NP_TC_HASH
-#define NP_TC_HASH 0
 #endif
 // The load that filters a child item before its atomic (level[v] for BFS,
 // dist(v) for SSSP). Only the atomic decides, and a stale value can only be
@@ -204,10 +186,6 @@ struct BodyArgs {
   const int* row_ptr;            // triangle counting: row bounds of a child's vertex
   unsigned long long* acc;       // triangle counting: kTcSlots partial counts
   unsigned long long* dtag;      // SSSP, packed form: dist << 32 | tag per vertex
-  // BFS: visited bitmap (bit v set once v is claimed) the children filter on
-  // instead of level[v], or NULL. At 2^20 vertices it is 128 KB, small enough
-  // to stay in an SM's L1, where level[] (4 MB) mostly misses.
-  unsigned* vbits;
   // SSSP, packed form: a 4-byte copy of each distance that relaxations filter
   // on instead of the 8-byte packed word, or NULL. It is lowered after every
   // 64-bit atomicMin that lowers the distance, so it is never below the

@@ -122,7 +122,8 @@ class np_batch_class(ctypes.Structure):
     _fields_ = [("log2_lo", ctypes.c_int32), ("instances", ctypes.c_int32), ("groups", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("vertices", ctypes.c_int64), ("edges", ctypes.c_int64),
                 ("config", np_config), ("tuned_ms", ctypes.c_double), ("candidates", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32)]
+                ("reserved2", ctypes.c_int32), ("device_launch_ms", ctypes.c_double),
+                ("device_launch_granularity", ctypes.c_int32), ("device_launch_threshold", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved") and k != "config"}
@@ -334,10 +335,12 @@ NP_NOALLOC_MAX_CURVES = 65536
 def np_bezier_noalloc(ctrl, ncurves: int, offsets, points, cap: int, cfg=None, stream=None,
                       check: bool = True) -> int:
     """Tessellation without a context and without any allocation, for callers that
-    cannot allocate device memory when they call (for example while a CUDA graph is
-    being captured). Scratch is a static device array sized for NP_NOALLOC_MAX_CURVES
-    curves; calls that overlap on the GPU race on it. Make the first call on a device
-    before any stream capture (it looks up and clears that array)."""
+    cannot allocate device memory when they call (their memory belongs to their own
+    pool or a fixed budget, or an allocation would stall a latency-critical loop).
+    Scratch is a static device array sized for NP_NOALLOC_MAX_CURVES curves; calls
+    that overlap on the GPU race on it. Make the first call on a device before any
+    stream capture (it looks up and clears that array). offsets[ncurves] reports the
+    outcome: the total, > cap on a capacity shortfall, -1 if a bounded wait gave up."""
     s = lib().np_bezier_noalloc(_ptr(ctrl), int(ncurves), _ptr(offsets), _ptr(points), int(cap),
                                 ctypes.byref(_cfg(cfg)), _stream(stream))
     return _check(s, "np_bezier_noalloc", check)

@@ -5,19 +5,7 @@ import numpy as np
 import torch
 
 from paper_2201_02789_gb300 import nestpar as npb
-
-
-class DevGraph:
-    """A generated CSR graph copied to the GPU, with its np_csr descriptor."""
-
-    def __init__(self, g, device="cuda:0"):
-        self.g = g
-        self.n, self.m = g.n, g.m
-        self.row_ptr = torch.from_numpy(np.ascontiguousarray(g.row_ptr)).to(device)
-        self.col = torch.from_numpy(np.ascontiguousarray(g.col) if g.m else np.zeros(1, np.int32)).to(device)
-        w = g.w if g.w is not None else np.ones(g.m, np.uint32)
-        self.w = torch.from_numpy(np.ascontiguousarray(w).view(np.int32) if g.m else np.zeros(1, np.int32)).to(device)
-        self.csr = npb.make_csr(self.row_ptr, self.col, self.w, n=g.n, m=g.m)
+from paper_2201_02789_gb300.devgraph import DevGraph  # noqa: F401  (re-exported for the tests)
 
 
 def bfs(ctx, dg: DevGraph, src: int, cfg, stats=False):

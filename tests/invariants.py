@@ -151,3 +151,11 @@ def bezier_tolerance_ok(got, ref, rel: float = 1e-5) -> tuple[bool, float]:
     ratio = np.abs(got - ref) / (rel * scale)
     worst = float(ratio.max()) if ratio.size else 0.0
     return worst <= 1.0, worst
+
+
+def bezier_relative_error(got, ref, floor: float = 1e-3) -> float:
+    """The largest strict relative error |g - r| / |r| over coordinates with |r| >= floor."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    big = np.abs(ref) >= floor
+    return float((np.abs(got - ref)[big] / np.abs(ref[big])).max()) if big.any() else 0.0

@@ -60,7 +60,7 @@ int main(void) {
   printf("np_body %zu %zu %zu\n", sizeof(np_body), offsetof(np_body, level), offsetof(np_body, cap));
   printf("np_profile %zu %zu %zu\n", sizeof(np_profile), offsetof(np_profile, levels), offsetof(np_profile, level_child_ms));
   printf("np_batch_options %zu %zu %zu\n", sizeof(np_batch_options), offsetof(np_batch_options, max_group_edges), offsetof(np_batch_options, config));
-  printf("np_batch_class %zu %zu %zu\n", sizeof(np_batch_class), offsetof(np_batch_class, config), offsetof(np_batch_class, candidates));
+  printf("np_batch_class %zu %zu %zu\n", sizeof(np_batch_class), offsetof(np_batch_class, config), offsetof(np_batch_class, device_launch_threshold));
   printf("np_server_options %zu %zu %zu\n", sizeof(np_server_options), offsetof(np_server_options, levels_per_step), offsetof(np_server_options, sssp_config));
   printf("np_query_info %zu %zu %zu\n", sizeof(np_query_info), offsetof(np_query_info, slot), offsetof(np_query_info, finish_step));
   return 0;
@@ -77,7 +77,7 @@ int main(void) {
         "np_body": (npb.np_body, "level", "cap"),
         "np_profile": (npb.np_profile, "levels", "level_child_ms"),
         "np_batch_options": (npb.np_batch_options, "max_group_edges", "config"),
-        "np_batch_class": (npb.np_batch_class, "config", "candidates"),
+        "np_batch_class": (npb.np_batch_class, "config", "device_launch_threshold"),
         "np_server_options": (npb.np_server_options, "levels_per_step", "sssp_config"),
         "np_query_info": (npb.np_query_info, "slot", "finish_step"),
     }

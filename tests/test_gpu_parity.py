@@ -13,7 +13,8 @@ import torch
 
 import oracle
 from gpu_util import DevGraph, bezier, bfs, form_grid, sssp
-from invariants import bezier_tolerance_ok, check_bfs_levels, check_sssp_dist, csr_from_edges
+from invariants import (bezier_relative_error, bezier_tolerance_ok, check_bfs_levels, check_sssp_dist,
+                        csr_from_edges)
 from paper_2201_02789_gb300 import gen
 from paper_2201_02789_gb300 import nestpar as npb
 
@@ -460,6 +461,11 @@ def test_rmat20_plain_cdp_full(ctx, rmat20):
 
 
 def test_bt64k_full(ctx):
+    """Full size, offsets exact and points within the scaled tolerance; the strict relative
+    error where |r| >= 1e-3 is reported. FP32 evaluation of B(t) errs by a few units of
+    2^-24 of the largest term (coordinates in [0, 1]), about 1e-7 absolute, so a coordinate
+    near 1e-3 can be off by about 1e-4 relative: the bound asserted there is the absolute
+    one, 16 * 2^-24 (about 1e-6), divided by |r|."""
     ctrl = gen.bt64k()
     ref_off, ref_pts = oracle.bezier(ctrl)
     status, off, pts, st = bezier(ctx, ctrl, npb.config("tca"), cap=int(ref_off[-1]))
@@ -467,6 +473,11 @@ def test_bt64k_full(ctx):
     np.testing.assert_array_equal(off, ref_off)
     ok, worst = bezier_tolerance_ok(pts, ref_pts)
     assert ok, worst
+    err = np.abs(pts.astype(np.float64) - ref_pts)
+    assert err.max() <= 16 * 2.0 ** -24, err.max()
+    rel = bezier_relative_error(pts, ref_pts, 1e-3)
+    print(f"bt64k: max |g - r| = {err.max():.3e}, max relative error where |r| >= 1e-3: {rel:.3e}")
+    assert rel <= 16 * 2.0 ** -24 / 1e-3
 
 
 def test_bench_tuned_configs_full(ctx, g4k):
