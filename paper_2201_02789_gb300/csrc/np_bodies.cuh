@@ -21,6 +21,7 @@ struct BfsBody {
   static constexpr bool kPushes = true;
   static constexpr bool kBalance = false;   // child blocks cost the same: static ranges
   static constexpr int kStage = 1;          // edge lists the child can stage: col
+  static constexpr int kWarpParentRegs = NP_WARP_PARENT_MAXREG;
   struct P {
     int base;
     int qbase;   // query part of the ids of this parent's children
@@ -69,6 +70,7 @@ struct SsspBody {
   static constexpr bool kPushes = true;
   static constexpr bool kBalance = false;
   static constexpr int kStage = 2;          // col and w
+  static constexpr int kWarpParentRegs = 96;   // (the stamp form spills at 80)
   struct P {
     int base;
     unsigned du;
@@ -178,6 +180,7 @@ struct TcBody {
   static constexpr bool kPushes = false;
   static constexpr bool kBalance = true;    // block cost varies with the lists' lengths
   static constexpr int kStage = 0;
+  static constexpr int kWarpParentRegs = NP_WARP_PARENT_MAXREG;
   struct P {
     int base;
     int n;
@@ -242,6 +245,7 @@ struct Sssp64Body {
   static constexpr bool kPushes = true;
   static constexpr bool kBalance = false;
   static constexpr int kStage = 2;          // col and w
+  static constexpr int kWarpParentRegs = NP_WARP_PARENT_MAXREG;
   struct P {
     int base;
     unsigned du;
@@ -314,6 +318,7 @@ struct BezierBody {
   static constexpr bool kPushes = false;
   static constexpr bool kBalance = false;
   static constexpr int kStage = 0;
+  static constexpr int kWarpParentRegs = 128;   // (32-byte parents: no cap below that without spills)
   struct P {
     float x0, y0, x1, y1, x2, y2;
     int base;

@@ -112,7 +112,10 @@ namespace nestpar {
 // at the end of every body in place of the condition kernel: it moves the base
 // on by the body's K levels, runs what it can, and sets the loop's condition
 // (iterations counted and capped only at the end of a body).
-constexpr int kSmallItems = 16384;
+#ifndef NP_SMALL_ITEMS
+#define NP_SMALL_ITEMS 16384
+#endif
+constexpr int kSmallItems = NP_SMALL_ITEMS;
 
 template <class Body>
 __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditionalHandle h, int K, int in_body) {

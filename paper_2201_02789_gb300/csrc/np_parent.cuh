@@ -260,7 +260,10 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
   const int ntiles = ceil_div(count, 32);
   // CTAs whose warps would all find no tile leave at once
   if ((int)blockIdx.x * ((int)blockDim.x >> 5) >= ntiles) return;
+  // the CTA's counters (np_stats), in shared memory: no registers held across the tile loop
+  __shared__ unsigned long long s_cnt[5];
   if (threadIdx.x == 0) *s_stage_n = 0;
+  if (threadIdx.x < 5) s_cnt[threadIdx.x] = 0ull;
   __syncthreads();
   const unsigned long long epoch = level_epoch(st, L);
   const int* ids = fixed ? a.ids : ((L & 1) ? a.fr1 : a.fr0);
@@ -271,7 +274,6 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
   const int T = a.threshold < 1 ? 1 : a.threshold;
   const int CB = a.child_block;
   StageSink sink{b.next, b.next_count, s_stage, s_stage_n};
-  unsigned long long n_par = 0, n_items = 0, n_serial = 0, n_launch = 0, n_citems = 0;
 
   // Without look-back waits (atomic aggregation scan, no output offsets) no
   // tile waits on another, so each warp's first tile is its own index and
@@ -347,13 +349,24 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
     }
     const bool launch = FORM == 1 && valid && N >= T;
     const bool serial = valid && !launch && N > 0;
-    n_par += __popc(__ballot_sync(kFull, valid));
-    n_items += __reduce_add_sync(kFull, (unsigned)N);
-    n_serial += __popc(__ballot_sync(kFull, serial));
+    {
+      const unsigned c_par = __popc(__ballot_sync(kFull, valid)), c_items = __reduce_add_sync(kFull, (unsigned)N);
+      const unsigned c_serial = __popc(__ballot_sync(kFull, serial));
+      if (lane == 0) {
+        atomicAdd(&s_cnt[0], (unsigned long long)c_par);
+        atomicAdd(&s_cnt[1], (unsigned long long)c_items);
+        atomicAdd(&s_cnt[2], (unsigned long long)c_serial);
+      }
+    }
     if constexpr (FORM == 1) {
       const unsigned lm = __ballot_sync(kFull, launch);
-      n_launch += __popc(lm);
-      n_citems += __reduce_add_sync(kFull, launch ? (unsigned)N : 0u);
+      {
+        const unsigned c_citems = __reduce_add_sync(kFull, launch ? (unsigned)N : 0u);
+        if (lane == 0 && lm) {
+          atomicAdd(&s_cnt[3], (unsigned long long)__popc(lm));
+          atomicAdd(&s_cnt[4], (unsigned long long)c_citems);
+        }
+      }
       const unsigned cg = launch ? (unsigned)ceil_div(ceil_div(N, CB), a.cfactor) : 0u;
       unsigned inc = cg;
 #pragma unroll
@@ -456,12 +469,13 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
     }
   }
   if constexpr (Body::kPushes) stage_flush(s_stage, s_stage_n, b.next, b.next_count, s_stage_base);
-  if (lane == 0) {
-    add_stat(st, S_PARENTS, n_par);
-    add_stat(st, S_ITEMS, n_items);
-    add_stat(st, S_SERIAL, n_serial);
-    add_stat(st, S_LAUNCHP, n_launch);
-    add_stat(st, S_CITEMS, n_citems);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    add_stat(st, S_PARENTS, s_cnt[0]);
+    add_stat(st, S_ITEMS, s_cnt[1]);
+    add_stat(st, S_SERIAL, s_cnt[2]);
+    add_stat(st, S_LAUNCHP, s_cnt[3]);
+    add_stat(st, S_CITEMS, s_cnt[4]);
   }
 }
 
@@ -663,7 +677,7 @@ __global__ void __maxnreg__(NP_CTA_PARENT_MAXREG) parent_cta(Args a) {
 }
 
 template <class Body, int FORM>
-__global__ void NP_PARENT_BOUNDS parent_warp(Args a) {
+__global__ void __maxnreg__(Body::kWarpParentRegs) parent_warp(Args a) {
   NP_PDL_ENTRY();
   __shared__ int s_stage[kCtaStage];
   __shared__ int s_stage_n, s_stage_base;

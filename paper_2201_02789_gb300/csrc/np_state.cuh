@@ -85,6 +85,12 @@
 #else
 #define NP_PARENT_BOUNDS __launch_bounds__(kMaxParentBlock)
 #endif
+// Register cap of the warp-tiled parent (spread serial loop) of the graph
+// bodies: at 80 it needs no spill and three 256-thread CTAs fit an SM instead
+// of two. (Each body states its own cap, kWarpParentRegs.)
+#ifndef NP_WARP_PARENT_MAXREG
+#define NP_WARP_PARENT_MAXREG 80
+#endif
 
 namespace nestpar {
 
