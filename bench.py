@@ -84,7 +84,11 @@ WORKLOADS = {
 # per-workload values of the aggregated form's knobs, from threshold x cfactor x child-block
 # sweeps on GB300 (the paper also tunes T and CF per benchmark); other workloads use the defaults
 TUNED = {# tessellation: 512-thread parent CTAs make the output-offset look-back groups 16 tiles long
-         "bt64k": dict(parent_block=512, child_block=32, cfactor=4), "tc-rmat17": dict(threshold=8, child_block=32, cfactor=1)}
+         "bt64k": dict(parent_block=512, child_block=32, cfactor=4), "tc-rmat17": dict(threshold=8, child_block=32, cfactor=1),
+         # SSSP: every grid level's children only reduce and a sweep over the vertex state forms the
+         # next frontier (A/B on GB300: 454 -> 436 us; BFS, whose claims rarely reach the atomic,
+         # loses 181 -> 187 us and keeps the appending frontier)
+         "sssp-rmat20": dict(sweep_parents=1)}
 # (the 4096-vertex graph, latency-bound, runs almost every level in the while driver's one-CTA
 # small-level loop: 115 us, against 150 us on the persistent level loop with 8 CTAs)
 

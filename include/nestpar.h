@@ -110,6 +110,16 @@ typedef int32_t np_status;
  *                     records in shared memory and searches there. */
 #define NP_SMALL_PARENTS_MAX 1024
 
+/* How a level loop forms the next frontier. By default children append each
+ * vertex they reach (the relaxation's or claim's atomic returns the old value
+ * to decide it; one atomic per warp batch reserves the places). With
+ * sweep_parents > 0 (np_bfs / np_sssp, grid-host aggregation with
+ * NP_SERIAL_SPREAD, graph / chunk / host driver), a level with at least that
+ * many parents instead has its children only reduce (a fire-and-forget atomic
+ * min of the level, or of the packed distance and tag), and a sweep over the
+ * vertex state after the level collects the vertices it reached, in vertex
+ * order. Other calls and forms append. */
+
 #define NP_SERIAL_SPREAD 0
 #define NP_SERIAL_PACKED 1
 #define NP_SERIAL_BLOCK 2
@@ -134,7 +144,9 @@ typedef struct np_config {
                             iteration one CTA runs whole levels itself while the frontier
                             has at most this many parents (<= NP_SMALL_PARENTS_MAX) and at
                             most 16384 children in all; 0 = off */
-  int32_t reserved[2];   /* must be zero */
+  int32_t sweep_parents; /* np_bfs / np_sssp: levels with at least this many parents form the
+                            next frontier by a sweep (see below); 0 = every level appends */
+  int32_t reserved[1];   /* must be zero */
 } np_config;
 
 /* Fills the library defaults: CDP, threshold 32, cfactor 4, grid-host

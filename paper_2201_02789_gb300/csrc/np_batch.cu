@@ -322,6 +322,7 @@ np_status np_batch_create(np_ctx* ctx, int32_t count, const np_csr* graphs, cons
     Class c;
     c.log2_lo = k;
     c.cfg = opt->config;
+    c.cfg.sweep_parents = 0;   // (the frontier sweep covers single solves)
     const int ci = (int)b->classes.size();
     Group* cur = nullptr;
     for (int i = 0; i < count; i++) {
@@ -455,6 +456,7 @@ np_status np_batch_set_config(np_batch* b, int32_t cls, const np_config* cfg) {
   if (!batch_form_ok(*cfg)) return NP_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lk(b->mu);
   b->classes[(size_t)cls].cfg = *cfg;
+  b->classes[(size_t)cls].cfg.sweep_parents = 0;
   b->classes[(size_t)cls].tuned_ms = 0.0;
   drop_batch_graph(b);
   return NP_OK;

@@ -3,7 +3,7 @@
 
 namespace nestpar {
 const BodyKernels& bfs_kernels() {
-  static const BodyKernels t = make_table<BfsBody>();
+  static const BodyKernels t = with_sweep<BfsSweepBody, 0>(make_table<BfsBody>());
   return t;
 }
 }  // namespace nestpar

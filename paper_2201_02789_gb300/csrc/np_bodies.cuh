@@ -312,6 +312,74 @@ struct Sssp64Body {
   }
 };
 
+// ------------------------------------------------ bodies of the swept frontier
+//
+// In a level with b.sweep set, the next frontier is rebuilt after the level
+// from the vertex state (a sweep over the vertices, see frontier_sweep_kernel)
+// instead of appended by the children. Nothing then waits on an atomic's
+// return: a child item's effect is a fire-and-forget reduction (red.min), and
+// the state alone tells which vertices level L reached: level[v] == L + 1
+// (BFS), tag(v) == L + 1 (packed SSSP: the last level that lowered dist(v)).
+// In other levels these bodies append as the queue bodies do.
+__device__ __forceinline__ void red_min_u32(unsigned* p, unsigned v) {
+  asm volatile("red.relaxed.gpu.global.min.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_min_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// BFS: level[] read as unsigned (unreached -1 = the largest value), so a claim
+// is min(level[v], L + 1): a vertex reached in an earlier level keeps its level,
+// whatever a stale filter read said.
+struct BfsSweepBody : BfsBody {
+  template <int K>
+  __device__ static void apply_batch(const BodyArgs& b, const P (&p)[K], const int (&i)[K], const F (&f)[K],
+                                     const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
+    if (!b.sweep) {
+      BfsBody::apply_batch<K>(b, p, i, f, valid, push, v);
+      return;
+    }
+    int cur[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      v[k] = f[k].v;
+      push[k] = false;
+      cur[k] = valid[k] ? NP_FILTER_LOAD(&b.level[v[k]]) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++)
+      if (valid[k] && cur[k] == -1) red_min_u32(reinterpret_cast<unsigned*>(&b.level[v[k]]), (unsigned)(b.L + 1));
+  }
+};
+
+// SSSP, packed form: the 64-bit min of (nd << 32 | L + 1) as a reduction; an
+// equal distance keeps the older, smaller tag, as in Sssp64Body.
+struct Sssp64SweepBody : Sssp64Body {
+  template <int K>
+  __device__ static void apply_batch(const BodyArgs& b, const P (&p)[K], const int (&i)[K], const F (&f)[K],
+                                     const bool (&valid)[K], bool (&push)[K], int (&v)[K]) {
+    if (!b.sweep) {
+      Sssp64Body::apply_batch<K>(b, p, i, f, valid, push, v);
+      return;
+    }
+    const unsigned tag = (unsigned)(b.L + 1);
+    unsigned long long nd[K], cur[K];
+    bool live[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      v[k] = f[k].v;
+      push[k] = false;
+      live[k] = p[k].du != 0xffffffffu;
+      const unsigned long long s = (unsigned long long)p[k].du + f[k].w;
+      nd[k] = ((s >= 0xffffffffull ? 0xfffffffeull : s) << 32) | tag;
+      cur[k] = (valid[k] && live[k]) ? NP_FILTER_LOAD(&b.dtag[v[k]]) : 0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++)
+      if (valid[k] && live[k] && (nd[k] >> 32) < (cur[k] >> 32)) red_min_u64(&b.dtag[v[k]], nd[k]);
+  }
+};
+
 // BT (Section VII): parent = quadratic curve; child item j = point j.
 struct BezierBody {
   static constexpr bool kOffsets = true;

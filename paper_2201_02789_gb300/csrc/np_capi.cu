@@ -73,6 +73,7 @@ np_status solve(np_ctx* c, int kind, const np_csr* g, int src, int* level, unsig
   a.b.level = level;
   a.b.dist = dist;
   a.b.stamp = wsp<int>(c->w, c->w.lay.off_stamp);
+  if (p.sweep) a.n_vertices = g->n;
   if (kind == 1) {
     NP_TRY(ensure_dtag(c, g->n));
     a.b.dtag = c->dtag;
@@ -135,7 +136,8 @@ np_status solve_multi(np_ctx* c, int kind, const np_csr* g, int nsrc, const int3
   }
   NP_CK(cudaMemcpyAsync(c->ids, ids.data(), sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, s));
   const BodyKernels& K = kind == 0 ? bfs_kernels() : sssp64_kernels();
-  const np_config mcfg = serial_for(*cfg, nsrc, g->m);
+  np_config mcfg = serial_for(*cfg, nsrc, g->m);
+  mcfg.sweep_parents = 0;   // (the sweep covers single solves)
   Plan p = make_plan(K, mcfg);
   Args a;
   base_args(c->w, mcfg, a);

@@ -478,10 +478,12 @@ __global__ void NP_CHILD_AGG_BOUNDS(CF) child_agg(BodyArgs b, AggSeg s) {
   if (s.mode != 0) {
     int L = b.L;
     if (s.level_mode) {
-      L = __ldcg(&b.st->base) + s.k;
+      int count = 0;
+      level_of(b.st, s.k, L, count);
       b.L = L;
       b.next = (L & 1) ? s.fr0 : s.fr1;
       b.next_count = &b.st->count[(L + 1) % 3];
+      b.sweep = s.sweep_parents > 0 && count >= s.sweep_parents;
     }
     agg_totals(b.st, L, s.mode, nrec, total);
   }

@@ -345,7 +345,8 @@ np_status check_config(const np_config* cfg) {
   if (cfg->serial != NP_SERIAL_SPREAD && cfg->serial != NP_SERIAL_PACKED && cfg->serial != NP_SERIAL_BLOCK)
     return NP_ERR_INVALID;
   if (cfg->small_parents < 0 || cfg->small_parents > NP_SMALL_PARENTS_MAX) return NP_ERR_INVALID;
-  for (int k = 0; k < 2; k++)
+  if (cfg->sweep_parents < 0) return NP_ERR_INVALID;
+  for (int k = 0; k < 1; k++)
     if (cfg->reserved[k] != 0) return NP_ERR_INVALID;
   return NP_OK;
 }
@@ -354,6 +355,11 @@ np_config serial_for(const np_config& cfg, int64_t copies, int64_t m) {
   np_config c = cfg;
   if (copies * m >= (int64_t)INT_MAX) c.serial = NP_SERIAL_SPREAD;
   return c;
+}
+
+bool sweeps(const np_config& cfg) {
+  return cfg.sweep_parents > 0 && cfg.variant == NP_VARIANT_CDP && cfg.granularity == NP_GRAN_GRID_HOST &&
+         cfg.serial == NP_SERIAL_SPREAD && cfg.driver != NP_DRIVER_PERSISTENT;
 }
 
 int serial_form(const np_config& cfg) {
@@ -380,6 +386,11 @@ Plan make_plan(const BodyKernels& K, const np_config& cfg) {
     p.child = form == NP_SERIAL_PACKED ? K.child_agg_pack[cfi] : K.child_agg[cfi];
     p.loop = K.level_loop_agg[cfi];
     p.small = cfg.small_parents > 0 ? K.level_small : nullptr;
+    if (sweeps(cfg) && K.parent_sweep) {
+      p.parent = K.parent_sweep;
+      p.child = K.child_sweep[cfi];
+      p.sweep = K.frontier_sweep;
+    }
     p.mode = M_GRID_HOST;
     p.gran = G_GRID_HOST;
   } else {
@@ -421,6 +432,7 @@ void base_args(const Workspace& w, const np_config& cfg, Args& a) {
   a.scan = cfg.scan;
   a.pack = serial_form(cfg) == NP_SERIAL_PACKED ? 1 : 0;
   a.small_parents = cfg.small_parents;
+  a.sweep_parents = sweeps(cfg) ? cfg.sweep_parents : 0;
   a.prec = wsp<int4>(w, w.lay.off_prec);
   a.pfirst = wsp<int>(w, w.lay.off_pfirst);
   a.b.st = w.st;
@@ -480,6 +492,7 @@ AggSeg make_seg(const Args& a, const Grids& g, bool level_mode) {
   seg.fr1 = a.fr1;
   seg.cb = g.cblock;
   seg.pack = a.pack;
+  seg.sweep_parents = a.sweep_parents;
   seg.prec = a.prec;
   seg.pfirst = a.pfirst;
   return seg;
@@ -497,6 +510,14 @@ BodyArgs child_body(const Args& a, bool level_mode) {
 
 }  // namespace
 
+// CTAs of the frontier sweep: kSweepVertices state elements each, at most as
+// many as the resident child grid (the sweep loops over the rest).
+int sweep_grid(const Args& a, const Grids& g) {
+  const int need = (a.n_vertices + kSweepVertices - 1) / kSweepVertices;
+  const int cap = g.cgrid > 0 ? g.cgrid : 1;
+  return need < 1 ? 1 : (need > cap ? cap : need);
+}
+
 // Enqueues the grids of one level (level mode, at body position k) or of one
 // fixed pass.
 np_status enqueue_pass(const Plan& p, Args a, const Grids& g, bool level_mode, int k, cudaStream_t s) {
@@ -511,6 +532,7 @@ np_status enqueue_pass(const Plan& p, Args a, const Grids& g, bool level_mode, i
     void* cargs[] = {&b, &seg};
     NP_CK(launch_pdl(p.child, dim3(g.cgrid), dim3(g.cthreads), cargs, s, pdl));
   }
+  if (p.sweep && level_mode) NP_CK(launch_pdl(p.sweep, dim3(sweep_grid(a, g)), dim3(256), pargs, s, pdl));
   return NP_OK;
 }
 
@@ -538,6 +560,8 @@ np_status profiled_pass(Engine& e, const Workspace& w, const Plan& p, Args a, co
     NP_CK(cudaLaunchKernel(p.child, dim3(g.cgrid), dim3(g.cthreads), cargs, 0, s));
     child = true;
   }
+  // (the frontier sweep counts with the child grid)
+  if (p.sweep && level_mode) NP_CK(cudaLaunchKernel(p.sweep, dim3(sweep_grid(a, g)), dim3(256), pargs, 0, s));
   NP_CK(cudaEventRecord(e.ev[2], s));
   if (level_mode) {
     advance_base_kernel<<<1, 1, 0, s>>>(w.st, 1);

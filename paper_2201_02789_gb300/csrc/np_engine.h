@@ -51,7 +51,8 @@ struct Plan {
   const void* parent = nullptr;
   const void* child = nullptr;  // persistent child grid (grid-host form)
   const void* loop = nullptr;   // persistent level loop (NODP and grid-host forms)
-  const void* small = nullptr;  // one-CTA small-level loop at the start of each while body (grid-host)
+  const void* small = nullptr;  // one-CTA small-level loop before the while loop and at each body's end (grid-host)
+  const void* sweep = nullptr;  // swept frontier: the kernel that rebuilds the next frontier after each level
   int mode = M_NODP;
   int gran = G_NODP;
 };
@@ -115,6 +116,10 @@ int serial_form(const np_config& cfg);
 // loop over `copies` traversals of a graph with m edges at once, which could
 // meet 2^31 items or more, takes the warp-tiled parent (SPREAD) instead.
 np_config serial_for(const np_config& cfg, int64_t copies, int64_t m);
+// The swept frontier under cfg: requested, grid-host aggregation with the
+// warp-tiled parent, not the persistent loop (np_bfs / np_sssp only; other
+// entry points run the appended frontier).
+bool sweeps(const np_config& cfg);
 Plan make_plan(const BodyKernels& K, const np_config& cfg);
 // Args of one level loop / pass over workspace `w` (vmask all ones).
 void base_args(const Workspace& w, const np_config& cfg, Args& a);

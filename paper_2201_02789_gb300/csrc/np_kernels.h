@@ -27,6 +27,11 @@ struct BodyKernels {
   const void* parent_cta;                     // parent_cta<Body>: grid-host, CTA tiles (serial modes BLOCK, PACKED)
   const void* child_agg_pack[kNumCF];         // child_agg_pack<Body, cf>: the child grid of PACKED
   const void* level_small;                    // level_small<Body>: one-CTA loop over small levels (or NULL)
+  // swept frontier (BFS and packed SSSP only, else NULL): the grid-host parent and
+  // child grids of the reducing body, and the sweep that rebuilds the frontier
+  const void* parent_sweep;
+  const void* child_sweep[kNumCF];
+  const void* frontier_sweep;
 };
 
 const BodyKernels& bfs_kernels();

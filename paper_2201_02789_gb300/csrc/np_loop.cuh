@@ -223,3 +223,58 @@ __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditional
 }
 
 }  // namespace nestpar
+
+namespace nestpar {
+
+// ------------------------------------------------------------- frontier sweep
+//
+// After level L of a swept-frontier form (children that only reduce, see
+// BfsSweepBody, Sssp64SweepBody): the next frontier is every vertex the level
+// reached, level[v] == L + 1 (BFS) or tag(v) == L + 1 (packed SSSP). Each CTA
+// takes kSweepVertices consecutive vertices (coalesced loads of the state),
+// scans its marks and reserves its part of the frontier with one atomic; ids
+// stay in vertex order within a CTA's range up to the interleaving of its
+// threads, which keeps the next level's row-bound loads close together.
+constexpr int kSweepVertices = 2048;
+
+template <int KIND>
+__global__ void __launch_bounds__(256) frontier_sweep_kernel(Args a) {
+  NP_PDL_ENTRY();
+  constexpr int KV = kSweepVertices / 256;
+  __shared__ uint2 s_scan[33];
+  __shared__ int s_base;
+  LevelState* st = a.st;
+  int L = 0, count = 0;
+  level_of(st, a.k, L, count);
+  // level L did not run, or its children appended the frontier themselves
+  if (count <= 0 || count < a.sweep_parents) return;
+  const int n = a.n_vertices;
+  const unsigned want = (unsigned)(L + 1);
+  int* next = (L & 1) ? a.fr0 : a.fr1;
+  int* next_count = &st->count[(L + 1) % 3];
+  for (int c0 = (int)blockIdx.x * kSweepVertices; c0 < n; c0 += (int)gridDim.x * kSweepVertices) {
+    bool mark[KV];
+    unsigned mine = 0;
+#pragma unroll
+    for (int k = 0; k < KV; k++) {
+      const int v = c0 + k * 256 + (int)threadIdx.x;
+      if (KIND == 0)
+        mark[k] = v < n && (unsigned)__ldcg(&a.b.level[v]) == want;
+      else
+        mark[k] = v < n && (unsigned)__ldcg(&a.b.dtag[v]) == want;
+      mine += mark[k] ? 1u : 0u;
+    }
+    unsigned ex, e1, tot, t1;
+    block_scan2(mine, 0u, ex, e1, tot, t1, s_scan);
+    if (tot == 0) continue;   // uniform over the CTA
+    if (threadIdx.x == 0) s_base = atomicAdd(next_count, (int)tot);
+    __syncthreads();
+    int pos = s_base + (int)ex;
+#pragma unroll
+    for (int k = 0; k < KV; k++)
+      if (mark[k]) next[pos++] = c0 + k * 256 + (int)threadIdx.x;
+    __syncthreads();   // s_base is rewritten by the next range's reservation
+  }
+}
+
+}  // namespace nestpar

@@ -26,7 +26,7 @@ __device__ __forceinline__ void launch_direct(const BodyArgs& b, int pid, int ba
 template <class Body, int CF>
 __device__ __forceinline__ void launch_aggregated(const BodyArgs& b, const int4* rec, const int* boff, int nrec,
                                                   int total, int child_block, unsigned* s_stat, CtaSink& sink) {
-  AggSeg s{rec, boff, nullptr, nullptr, nrec, total, 0, 0, 0, child_block, 0, nullptr, nullptr};   // a fixed segment
+  AggSeg s{rec, boff, nullptr, nullptr, nrec, total, 0, 0, 0, child_block, 0, nullptr, nullptr, 0, 0};   // a fixed segment
   child_agg<Body, CF><<<total, child_block, 0, cudaStreamFireAndForget>>>(b, s);
   if (cudaGetLastError() != cudaSuccess) {
     // run the aggregated grid's work in this thread: parent by parent, serially
@@ -271,6 +271,7 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
   b.L = L;
   b.next = fixed ? a.next_ovr : ((L & 1) ? a.fr0 : a.fr1);
   b.next_count = fixed ? a.next_count_ovr : &st->count[(L + 1) % 3];
+  b.sweep = !fixed && a.sweep_parents > 0 && count >= a.sweep_parents;
   const int T = a.threshold < 1 ? 1 : a.threshold;
   const int CB = a.child_block;
   StageSink sink{b.next, b.next_count, s_stage, s_stage_n};

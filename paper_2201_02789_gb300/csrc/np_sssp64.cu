@@ -3,7 +3,7 @@
 
 namespace nestpar {
 const BodyKernels& sssp64_kernels() {
-  static const BodyKernels t = make_table<Sssp64Body>();
+  static const BodyKernels t = with_sweep<Sssp64SweepBody, 1>(make_table<Sssp64Body>());
   return t;
 }
 }  // namespace nestpar

@@ -197,6 +197,8 @@ struct BodyArgs {
   // 64-bit atomicMin that lowers the distance, so it is never below the
   // distance: a relaxation it rejects could not have lowered it either.
   unsigned* dmirror;
+  int sweep;                     // 1: this level's children reduce, the frontier sweep appends
+  int pad;
 };
 
 struct Args {
@@ -237,7 +239,9 @@ struct Args {
   int4* prec;
   int* pfirst;
   int small_parents;             // > 0: the while body's one-CTA loop runs levels of at most this many parents
-  int pad2;
+  int n_vertices;                // swept frontier: state elements the sweep visits
+  int sweep_parents;             // swept frontier: levels with at least this many parents sweep (0 = none)
+  int pad3;
 };
 
 struct AggSeg {
@@ -254,6 +258,8 @@ struct AggSeg {
   int pack;                      // 1: also run the packed serial children (prec, pfirst)
   const int4* prec;
   const int* pfirst;
+  int sweep_parents;             // level mode: levels with at least this many parents sweep (0 = none)
+  int pad;
 };
 
 // ---------------------------------------------------------------- primitives

@@ -51,4 +51,17 @@ inline BodyKernels make_table() {
   return t;
 }
 
+// Adds the swept-frontier kernels of body S (state kind KIND) to a table.
+template <class S, int KIND>
+inline BodyKernels with_sweep(BodyKernels t) {
+  t.parent_sweep = (const void*)parent_warp<S, 1>;
+  t.child_sweep[0] = (const void*)child_agg<S, 1>;
+  t.child_sweep[1] = (const void*)child_agg<S, 2>;
+  t.child_sweep[2] = (const void*)child_agg<S, 4>;
+  t.child_sweep[3] = (const void*)child_agg<S, 8>;
+  t.child_sweep[4] = (const void*)child_agg<S, 16>;
+  t.frontier_sweep = (const void*)frontier_sweep_kernel<KIND>;
+  return t;
+}
+
 }  // namespace nestpar

@@ -49,7 +49,7 @@ class np_config(ctypes.Structure):
                 ("parent_block", ctypes.c_int32), ("scan", ctypes.c_int32), ("driver", ctypes.c_int32),
                 ("unroll", ctypes.c_int32), ("parent_grid", ctypes.c_int32),
                 ("serial", ctypes.c_int32), ("small_parents", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("sweep_parents", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
     def replace(self, **kw) -> "np_config":
         c = np_config()

@@ -45,7 +45,9 @@ def form_grid():
              ("griddev", npb.NP_GRAN_GRID_DEVICE, {}),
              ("gridhost-spread", npb.NP_GRAN_GRID_HOST, {"serial": npb.NP_SERIAL_SPREAD}),
              ("gridhost-block", npb.NP_GRAN_GRID_HOST, {"serial": npb.NP_SERIAL_BLOCK}),
-             ("gridhost-packed", npb.NP_GRAN_GRID_HOST, {"serial": npb.NP_SERIAL_PACKED})]
+             ("gridhost-packed", npb.NP_GRAN_GRID_HOST, {"serial": npb.NP_SERIAL_PACKED}),
+             # (the small-level loop off, so that the grids and the sweep run every level)
+             ("gridhost-sweep", npb.NP_GRAN_GRID_HOST, {"sweep_parents": 1, "small_parents": 0})]
     for gname, gran, extra in grans:
         scans = ([("", npb.NP_SCAN_ATOMIC), ("-lb", npb.NP_SCAN_LOOKBACK)]
                  if gran in (npb.NP_GRAN_MULTIBLOCK, npb.NP_GRAN_GRID_DEVICE, npb.NP_GRAN_GRID_HOST) else [("", npb.NP_SCAN_ATOMIC)])

@@ -112,6 +112,19 @@ EXTRA = [
     ("block-never", dict(serial=npb.NP_SERIAL_BLOCK, threshold=npb.INT32_MAX)),
     ("block-driver-host", dict(serial=npb.NP_SERIAL_BLOCK, driver=npb.NP_DRIVER_HOST, threshold=32)),
     ("block-driver-while1", dict(serial=npb.NP_SERIAL_BLOCK, driver=npb.NP_DRIVER_WHILE, unroll=1)),
+    # the swept frontier: drivers, the small-level loop around it, forms that fall back to the queue
+    ("sweep-small", dict(sweep_parents=1)),
+    ("sweep-small1", dict(sweep_parents=1, small_parents=1, unroll=1)),
+    ("sweep-driver-host", dict(sweep_parents=1, driver=npb.NP_DRIVER_HOST, small_parents=0)),
+    ("sweep-driver-chunk5", dict(sweep_parents=1, driver=npb.NP_DRIVER_CHUNK, unroll=5)),
+    ("sweep-grid1-lb", dict(sweep_parents=1, parent_grid=1, scan=npb.NP_SCAN_LOOKBACK,
+                            small_parents=0)),
+    ("sweep-cb1024", dict(sweep_parents=1, child_block=1024, cfactor=1, small_parents=0)),
+    ("sweep-persistent", dict(sweep_parents=1, driver=npb.NP_DRIVER_PERSISTENT)),
+    ("sweep-block", dict(sweep_parents=1, serial=npb.NP_SERIAL_BLOCK, small_parents=0)),
+    # levels above the limit sweep, the others append, in one solve
+    ("sweep-mixed100", dict(sweep_parents=100, small_parents=0)),
+    ("sweep-mixed400-lb-T4", dict(sweep_parents=400, small_parents=0, scan=npb.NP_SCAN_LOOKBACK, threshold=4)),
     ("spread-driver-while", dict(serial=npb.NP_SERIAL_SPREAD, driver=npb.NP_DRIVER_WHILE, threshold=32)),
     ("spread-grid3", dict(serial=npb.NP_SERIAL_SPREAD, parent_grid=3, threshold=16)),
 ]
@@ -198,13 +211,14 @@ EDGE = _edge_graphs()
 
 @pytest.mark.parametrize("gname", list(EDGE))
 @pytest.mark.parametrize("form", ["nodp", "cdp", "tc", "tca", "mb", "block", "persist", "persist-nodp",
-                                  "tca-nosmall", "tca-small1", "tca-small33-cta"])
+                                  "tca-nosmall", "tca-small1", "tca-small33-cta", "tca-sweep"])
 def test_edge_graphs(ctx, gname, form):
     g = EDGE[gname]
     kw = {"mb": dict(granularity="multiblock", group_blocks=2, threshold=4),
           "tca-nosmall": dict(small_parents=0),
           "tca-small1": dict(small_parents=1, unroll=1),
           "tca-small33-cta": dict(small_parents=33, serial=npb.NP_SERIAL_BLOCK, unroll=3),
+          "tca-sweep": dict(sweep_parents=1, small_parents=64),
           "block": dict(granularity="block", threshold=1, cfactor=2),
           "persist": dict(driver=npb.NP_DRIVER_PERSISTENT, threshold=2),
           "persist-nodp": dict(driver=npb.NP_DRIVER_PERSISTENT)}.get(form, {})
@@ -435,7 +449,8 @@ def rmat20():
 
 
 @pytest.mark.parametrize("form", ["tca", "nodp", "tca-mb", "tca-atomic", "tca-persistent", "nodp-persistent",
-                                  "tca-block", "tca-packed", "tca-block-lookback"])
+                                  "tca-block", "tca-packed", "tca-block-lookback", "tca-sweep",
+                                  "tca-sweep-nosmall", "tca-sweep-mixed"])
 def test_rmat20_sssp_bfs_full(ctx, rmat20, form):
     g, dg = rmat20
     kw = {"tca-mb": dict(granularity="multiblock", group_blocks=8),
@@ -443,6 +458,9 @@ def test_rmat20_sssp_bfs_full(ctx, rmat20, form):
           "tca-block": dict(serial=npb.NP_SERIAL_BLOCK),
           "tca-packed": dict(serial=npb.NP_SERIAL_PACKED),
           "tca-block-lookback": dict(serial=npb.NP_SERIAL_BLOCK, scan=npb.NP_SCAN_LOOKBACK, threshold=256),
+          "tca-sweep": dict(sweep_parents=1),
+          "tca-sweep-nosmall": dict(sweep_parents=1, small_parents=0),
+          "tca-sweep-mixed": dict(sweep_parents=100000, small_parents=0),
           "tca-persistent": dict(driver=npb.NP_DRIVER_PERSISTENT),
           "nodp-persistent": dict(driver=npb.NP_DRIVER_PERSISTENT)}.get(form, {})
     cfg = npb.config(form.split("-")[0], **kw)
