@@ -282,21 +282,13 @@ struct Sssp64Body {
     const unsigned tag = (unsigned)(b.L + 1);
     unsigned long long nd[K], cur[K];
     bool live[K];
-    const bool mirror = NP_SSSP_MIRROR && b.dmirror != nullptr;
 #pragma unroll
     for (int k = 0; k < K; k++) {
       v[k] = f[k].v;
       live[k] = p[k].du != 0xffffffffu;
       const unsigned long long s = (unsigned long long)p[k].du + f[k].w;
       nd[k] = ((s >= 0xffffffffull ? 0xfffffffeull : s) << 32) | tag;
-#if NP_SSSP_PRECHECK
-      if (mirror)
-        cur[k] = (valid[k] && live[k]) ? (unsigned long long)NP_FILTER_LOAD(&b.dmirror[v[k]]) << 32 : 0ull;
-      else
-        cur[k] = (valid[k] && live[k]) ? NP_FILTER_LOAD(&b.dtag[v[k]]) : 0ull;
-#else
-      cur[k] = 0xffffffffffffffffull;
-#endif
+      cur[k] = (valid[k] && live[k]) ? NP_FILTER_LOAD(&b.dtag[v[k]]) : 0ull;
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -304,11 +296,8 @@ struct Sssp64Body {
       if (push[k]) cur[k] = atomicMin(&b.dtag[v[k]], nd[k]);
     }
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-      const bool lowered = push[k] && (nd[k] >> 32) < (cur[k] >> 32);
-      if (mirror && lowered) atomicMin(&b.dmirror[v[k]], (unsigned)(nd[k] >> 32));
-      push[k] = lowered && (unsigned)cur[k] != tag;
-    }
+    for (int k = 0; k < K; k++)
+      push[k] = push[k] && (nd[k] >> 32) < (cur[k] >> 32) && (unsigned)cur[k] != tag;
   }
 };
 

@@ -77,13 +77,11 @@ np_status solve(np_ctx* c, int kind, const np_csr* g, int src, int* level, unsig
   if (kind == 1) {
     NP_TRY(ensure_dtag(c, g->n));
     a.b.dtag = c->dtag;
-    // the caller's distance array holds the filter copy until the result overwrites it
-    if (NP_SSSP_MIRROR) a.b.dmirror = dist;
   }
   const int blocks = (int)((g->n + 255) / 256 < 4096 ? (g->n + 255) / 256 : 4096);
   if (c->e.profile) NP_CK(cudaEventRecord(c->e.ev[0], s));
   if (kind == 1)
-    init_dtag_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, g->n, src, c->dtag, a.fr0, g->n + 2, a.b.dmirror);
+    init_dtag_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, g->n, src, c->dtag, a.fr0, g->n + 2);
   else
     init_solve_kernel<<<blocks, 256, 0, s>>>(c->w.st, kind, g->n, src, level, dist, a.b.stamp, a.fr0, g->n + 2);
   NP_CK(cudaGetLastError());

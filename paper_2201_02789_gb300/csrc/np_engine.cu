@@ -161,11 +161,9 @@ __global__ void seed_dtag_kernel(LevelState* st, const int* ids, int nsrc, unsig
 }
 
 __global__ void init_dtag_solve_kernel(LevelState* st, int n, int src, unsigned long long* dtag, int* fr0,
-                                       int max_levels, unsigned* mirror) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+                                       int max_levels) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
     dtag[v] = v == src ? 0ull : 0xffffffff00000000ull;
-    if (mirror) mirror[v] = v == src ? 0u : 0xffffffffu;
-  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     fr0[0] = src;
     st->base = 0;
@@ -560,10 +558,10 @@ np_status profiled_pass(Engine& e, const Workspace& w, const Plan& p, Args a, co
     NP_CK(cudaLaunchKernel(p.child, dim3(g.cgrid), dim3(g.cthreads), cargs, 0, s));
     child = true;
   }
-  // (the frontier sweep counts with the child grid)
-  if (p.sweep && level_mode) NP_CK(cudaLaunchKernel(p.sweep, dim3(sweep_grid(a, g)), dim3(256), pargs, 0, s));
   NP_CK(cudaEventRecord(e.ev[2], s));
   if (level_mode) {
+    // the frontier sweep counts with the level bookkeeping ("other")
+    if (p.sweep) NP_CK(cudaLaunchKernel(p.sweep, dim3(sweep_grid(a, g)), dim3(256), pargs, 0, s));
     advance_base_kernel<<<1, 1, 0, s>>>(w.st, 1);
     NP_CK(cudaGetLastError());
     other = true;

@@ -176,10 +176,9 @@ __global__ void init_dtag_kernel(long long total, unsigned long long* dtag);
 __global__ void seed_dtag_kernel(LevelState* st, const int* ids, int nsrc, unsigned long long* dtag, int* fr0,
                                  int max_levels);
 __global__ void dtag_to_dist_kernel(long long total, const unsigned long long* dtag, unsigned* dist);
-// Single-source start of the packed form in one kernel (as init_solve_kernel);
-// mirror (nullable): the 4-byte distance copy relaxations filter on.
+// Single-source start of the packed form in one kernel (as init_solve_kernel).
 __global__ void init_dtag_solve_kernel(LevelState* st, int n, int src, unsigned long long* dtag, int* fr0,
-                                       int max_levels, unsigned* mirror);
+                                       int max_levels);
 // *out (+)= the sum of part[0, n) (one block)
 __global__ void sum_u64_kernel(const unsigned long long* part, int n, unsigned long long* out, int accumulate);
 // Sets *bad when a CSR breaks its contract: row_ptr[0] != 0, row_ptr[n] != m,

@@ -60,17 +60,6 @@
 #else
 #define NP_FILTER_LOAD(p) __ldcg(p)
 #endif
-// 1: a relaxation reads dist(v) first and issues the atomic only when it would
-// lower it; 0: every relaxation issues the atomic (one dependent round trip
-// fewer, more atomics)
-#ifndef NP_SSSP_PRECHECK
-#define NP_SSSP_PRECHECK 1
-#endif
-// 1: whole SSSP solves filter relaxations on a 4-byte distance copy kept in
-// the caller's output array during the solve (BodyArgs::dmirror)
-#ifndef NP_SSSP_MIRROR
-#define NP_SSSP_MIRROR 0
-#endif
 #ifdef NP_CHILD_MAXREG
 #define NP_CHILD_BOUNDS __maxnreg__(NP_CHILD_MAXREG)
 #define NP_CHILD_AGG_BOUNDS(CF) __maxnreg__(NP_CHILD_MAXREG)
@@ -192,11 +181,6 @@ struct BodyArgs {
   const int* row_ptr;            // triangle counting: row bounds of a child's vertex
   unsigned long long* acc;       // triangle counting: kTcSlots partial counts
   unsigned long long* dtag;      // SSSP, packed form: dist << 32 | tag per vertex
-  // SSSP, packed form: a 4-byte copy of each distance that relaxations filter
-  // on instead of the 8-byte packed word, or NULL. It is lowered after every
-  // 64-bit atomicMin that lowers the distance, so it is never below the
-  // distance: a relaxation it rejects could not have lowered it either.
-  unsigned* dmirror;
   int sweep;                     // 1: this level's children reduce, the frontier sweep appends
   int pad;
 };

@@ -35,7 +35,8 @@ def forms():
             ("block", npb.config("tca", granularity="block", threshold=2, cfactor=2)),
             ("serial-block", npb.config("tca", serial=npb.NP_SERIAL_BLOCK)),
             ("serial-packed", npb.config("tca", serial=npb.NP_SERIAL_PACKED, threshold=64)),
-            ("no-small-loop", npb.config("tca", small_parents=0))]
+            ("no-small-loop", npb.config("tca", small_parents=0)),
+            ("swept-frontier", npb.config("tca", sweep_parents=1, small_parents=0))]
     return out
 
 

@@ -1,9 +1,12 @@
-"""Build options that are off by default, built and checked against the oracle.
+"""Build options that select another code path than the default, built and checked
+against the oracle.
 
 NP_TMA_STAGE=1 stages each aggregated child block's edge lists in shared memory
-with the bulk-copy engine (cp.async.bulk into an mbarrier), one block ahead. The
-variant library is built in-tree beside the default one and exercised in its own
-process by tests/option_check.py, bit-exact against the oracle.
+with the bulk-copy engine (cp.async.bulk into an mbarrier), one block ahead.
+NP_PDL=0 launches the level loop's kernels without programmatic dependent
+launch; NP_FILTER_L1=0 reads the child items' filter values through L2 only.
+Each variant library is built in-tree beside the default one and exercised in
+its own process by tests/option_check.py, bit-exact against the oracle.
 """
 import os
 import subprocess
@@ -14,7 +17,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-OPTIONS = {"tma_stage": ("NP_TMA_STAGE=1",)}
+OPTIONS = {"tma_stage": ("NP_TMA_STAGE=1",), "no_pdl_l2_filter": ("NP_PDL=0", "NP_FILTER_L1=0")}
 
 
 @pytest.mark.parametrize("name", list(OPTIONS))
