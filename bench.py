@@ -83,8 +83,10 @@ WORKLOADS = {
 
 # per-workload values of the aggregated form's knobs, from threshold x cfactor x child-block
 # sweeps on GB300 (the paper also tunes T and CF per benchmark); other workloads use the defaults
-TUNED = {# tessellation: 512-thread parent CTAs make the output-offset look-back groups 16 tiles long
-         "bt64k": dict(parent_block=512, child_block=32, cfactor=4), "tc-rmat17": dict(threshold=8, child_block=32, cfactor=1),
+TUNED = {# tessellation: 512-thread parent CTAs make the output-offset look-back groups 16 tiles long;
+         # the curves below the threshold spread over the parent CTA (44.1 against 45.2 us)
+         "bt64k": dict(parent_block=512, child_block=32, cfactor=4, serial=2),   # serial 2: NP_SERIAL_BLOCK
+         "tc-rmat17": dict(threshold=8, child_block=32, cfactor=1),
          # SSSP: every grid level's children only reduce and a sweep over the vertex state forms the
          # next frontier (A/B on GB300: 454 -> 436 us; BFS, whose claims rarely reach the atomic,
          # loses 181 -> 187 us and keeps the appending frontier)
