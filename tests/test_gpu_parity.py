@@ -500,9 +500,10 @@ def test_bt64k_full(ctx):
 
 def test_bench_tuned_configs_full(ctx, g4k):
     """The configurations bench.py times where they differ from the library default (BT-64K
-    with 512-thread parent CTAs, 32-thread child blocks and CF 4; the triangle-counting
-    setting is checked in its own tests), and the 4096-vertex graph on the persistent loop
-    with 8 CTAs, which it used to time, at full size, against the oracle."""
+    with 512-thread parent CTAs, 32-thread child blocks, CF 4 and the serial children spread
+    over the parent CTA; the SSSP setting, the swept frontier, runs in test_rmat20_sssp_bfs_full
+    and the triangle-counting one in its own tests), and the 4096-vertex graph on the
+    persistent loop with 8 CTAs, at full size, against the oracle."""
     import bench
     cfg = npb.config("tca", **bench.TUNED["bt64k"])
     ctrl = gen.bt64k()
