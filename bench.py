@@ -644,8 +644,8 @@ def run_ours(args, ws, rank, local):
         return
 
     # kernels launched per solve: graph solves launch init (+ the small-level loop once before
-    # the while loop) + per while-body iteration `unroll` x (parent, child) + the condition
-    # kernel (the small-level loop); a tessellation launches init, parent and child
+    # the while loop) + per while-body iteration `unroll` x (parent, child[, sweep]) + the
+    # condition kernel (the small-level loop); a tessellation launches init, parent and child
     if wl["kind"] == "bezier":
         per_solve = 3
     elif wl["kind"] == "tc":
@@ -653,7 +653,9 @@ def run_ours(args, ws, rank, local):
     else:
         # init + while-body iterations x (unroll x (parent, child) + condition) (+ the SSSP
         # distances written from the packed state)
-        loop = 1 if cfg.driver == npb.NP_DRIVER_PERSISTENT else st["graph_iterations"] * (2 * cfg.unroll + 1)
+        # (the swept frontier adds its sweep kernel to every grid level)
+        per_level = 3 if cfg.sweep_parents > 0 else 2
+        loop = 1 if cfg.driver == npb.NP_DRIVER_PERSISTENT else st["graph_iterations"] * (per_level * cfg.unroll + 1)
         pre = 1 if cfg.driver != npb.NP_DRIVER_PERSISTENT and cfg.small_parents > 0 else 0
         per_solve = 1 + pre + loop + (1 if wl["kind"] == "sssp" else 0)
     gpu_launches = int(per_solve * args.steps)
