@@ -108,7 +108,7 @@ typedef int32_t np_status;
  *                     them ({parent, start, N, first item}), and each child
  *                     CTA takes chunks of 1024 items, stages the chunk's
  *                     records in shared memory and searches there. */
-#define NP_SMALL_PARENTS_MAX 1024
+#define NP_SMALL_PARENTS_MAX 2048
 
 /* How a level loop forms the next frontier. By default children append each
  * vertex they reach (the relaxation's or claim's atomic returns the old value
@@ -140,8 +140,8 @@ typedef struct np_config {
   int32_t unroll;        /* levels per graph chunk or per while-body, 1..16 */
   int32_t parent_grid;   /* persistent parent CTAs; 0 = resident capacity */
   int32_t serial;        /* NP_SERIAL_*: where the children of parents below the threshold run */
-  int32_t small_parents; /* grid-host form, while driver: at the start of each while-body
-                            iteration one CTA runs whole levels itself while the frontier
+  int32_t small_parents; /* grid-host form, while driver: before the while loop and at the end
+                            of each body one CTA runs whole levels itself while the frontier
                             has at most this many parents (<= NP_SMALL_PARENTS_MAX) and at
                             most 16384 children in all; 0 = off */
   int32_t sweep_parents; /* np_bfs / np_sssp: levels with at least this many parents form the

@@ -101,9 +101,9 @@ namespace nestpar {
 // kernel boundaries and a dependent chain of L2 round trips in each grid.
 // Under the conditional-while driver of the grid-host form this one-CTA kernel
 // runs whole levels itself while the frontier holds at most a.small_parents
-// (<= blockDim.x) parents with at most kSmallItems children in all: each
-// thread takes one parent (count, row bounds), a CTA scan gives the items'
-// offsets, the parents are staged in shared memory, and the CTA's threads take
+// (<= 2 * blockDim.x) parents with at most kSmallItems children in all: each
+// thread takes two consecutive parents (count, row bounds), a CTA scan gives the
+// items' offsets, the parents are staged in shared memory, and the CTA's threads take
 // the items, each finding its parent by a binary search over the staged
 // offsets; CTA barriers separate the levels. It keeps the level state as the
 // parent and child grids do (slots and the count two levels ahead cleared,
@@ -121,14 +121,17 @@ template <class Body>
 __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditionalHandle h, int K, int in_body) {
   NP_PDL_ENTRY();
   constexpr int KS = 4;
-  __shared__ int s_first[1024];
-  __shared__ int4 s_rec[1024];
+  constexpr int PPT = 2;   // parents per thread: thread t takes parents 2t and 2t + 1
+  __shared__ int s_first[PPT * 1024];
+  __shared__ int s_pid[PPT * 1024];
+  __shared__ int s_base[PPT * 1024];
+  __shared__ unsigned s_aux[PPT * 1024];
   __shared__ uint2 s_scan[33];
   __shared__ int s_stage[kCtaStage];
   __shared__ int s_stage_n, s_stage_base;
   LevelState* st = a.st;
   const int tid = (int)threadIdx.x, nt = (int)blockDim.x;
-  const int limit = a.small_parents < nt ? a.small_parents : nt;
+  const int limit = a.small_parents < PPT * nt ? a.small_parents : PPT * nt;
   const int max_levels = __ldcg(&st->max_levels);
   const int L0 = __ldcg(&st->base) + K;
   int L = L0;
@@ -139,12 +142,21 @@ __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditional
     const int count = __ldcg(&st->count[L % 3]);
     if (count <= 0 || count > limit || L >= max_levels) break;
     const int* ids = (L & 1) ? a.fr1 : a.fr0;
-    int pid = 0, base = 0, N = 0;
-    if (tid < count) pid = __ldcg(&ids[tid]);
-    const bool valid = tid < count && pid >= 0;
-    if (valid) Body::count(a, pid, base, N);
+    int pid[PPT], base[PPT], N[PPT];
+    bool valid[PPT];
+    unsigned mine = 0;
+#pragma unroll
+    for (int r = 0; r < PPT; r++) {
+      const int i = PPT * tid + r;
+      pid[r] = i < count ? __ldcg(&ids[i]) : 0;
+      valid[r] = i < count && pid[r] >= 0;
+      base[r] = 0;
+      N[r] = 0;
+      if (valid[r]) Body::count(a, pid[r], base[r], N[r]);
+      mine += (unsigned)N[r];
+    }
     unsigned e0, e1, items, t1;
-    block_scan2((unsigned)N, 0u, e0, e1, items, t1, s_scan);
+    block_scan2(mine, 0u, e0, e1, items, t1, s_scan);
     if (items > (unsigned)kSmallItems) break;   // uniform: the grids take this level
     if (tid == 0) {
       level_open(st, L, count);
@@ -154,11 +166,21 @@ __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditional
     b.L = L;
     b.next = (L & 1) ? a.fr0 : a.fr1;
     b.next_count = &st->count[(L + 1) % 3];
-    if (tid < count) {
+    {
       // parents without children keep a slot: the search takes the last parent
       // whose first item is <= t, which is the one holding t
-      s_first[tid] = (int)e0;
-      s_rec[tid] = make_int4(pid, base, N, valid ? (int)Body::aux(b, pid) : 0);
+      unsigned first = e0;
+#pragma unroll
+      for (int r = 0; r < PPT; r++) {
+        const int i = PPT * tid + r;
+        if (i < count) {
+          s_first[i] = (int)first;
+          s_pid[i] = pid[r];
+          s_base[i] = base[r];
+          s_aux[i] = valid[r] ? Body::aux(b, pid[r]) : 0u;
+        }
+        first += (unsigned)N[r];
+      }
     }
     __syncthreads();
     StageSink sink{b.next, b.next_count, s_stage, &s_stage_n};
@@ -176,9 +198,9 @@ __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditional
         int r = 0;
         for (int step = top; step > 0; step >>= 1)
           if (r + step < count && s_first[r + step] <= t) r += step;
-        const int4 q = s_rec[r];
         idx[k] = t - s_first[r];
-        pk[k] = Body::parent_aux(b, q.x, q.y, q.z, (unsigned)q.w);
+        // (the level-loop bodies do not use N in parent_aux)
+        pk[k] = Body::parent_aux(b, s_pid[r], s_base[r], 0, s_aux[r]);
         f[k] = v[k] ? Body::fetch(b, pk[k], idx[k]) : typename Body::F{};
       }
       bool pf[KS];
@@ -188,9 +210,12 @@ __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditional
     }
     // appends reach the next frontier and its count before the next level reads them
     if constexpr (Body::kPushes) stage_flush(s_stage, &s_stage_n, b.next, b.next_count, &s_stage_base);
-    n_par += valid ? 1u : 0u;
-    n_items += (unsigned)N;
-    n_serial += N > 0 ? 1u : 0u;
+#pragma unroll
+    for (int r = 0; r < PPT; r++) {
+      n_par += valid[r] ? 1u : 0u;
+      n_items += (unsigned)N[r];
+      n_serial += N[r] > 0 ? 1u : 0u;
+    }
     __syncthreads();
     L++;
   }

@@ -182,10 +182,10 @@ def _edge_graphs():
 
 
 def _switch_graph():
-    """Levels that cross the one-CTA small-level loop's limits (1024 parents, 16384
-    children) in both directions, twice: a short path, a vertex with 20000 children,
-    a level of 20000 parents funnelling into 600, a path again, a fan-out of 30000,
-    and a path tail."""
+    """Levels that cross the one-CTA small-level loop's limits (1024 or 2048 parents,
+    16384 children) in both directions, twice: a short path, a vertex with 20000
+    children, a level of 20000 parents funnelling into 600, a path again, a fan-out of
+    30000, a path, and a level of 1500 parents (above 1024, within 2048)."""
     rng = np.random.default_rng(77)
     edges = [(0, 1), (1, 2)]
     a0 = 3
@@ -200,8 +200,12 @@ def _switch_graph():
     e0 = d0 + 30000
     edges += [(d0 + i, e0 + i % 40) for i in range(30000)]      # 30000 parents, 40 children each way
     edges += [(e0 + i, e0 + 40) for i in range(40)]
-    edges += [(e0 + 40 + i, e0 + 41 + i) for i in range(8)]     # path tail
-    n = e0 + 49
+    edges += [(e0 + 40 + i, e0 + 41 + i) for i in range(8)]     # path
+    f0 = e0 + 49
+    edges += [(e0 + 48, f0 + i) for i in range(1500)]           # 1 parent, 1500 children
+    edges += [(f0 + i, f0 + 1500 + i % 7) for i in range(1500)]  # 1500 parents: one thread, two parents
+    edges += [(f0 + 1500 + i, f0 + 1507) for i in range(7)]
+    n = f0 + 1508
     ws = [int(x) for x in rng.integers(1, 256, size=len(edges))]
     return _graph_from_edges(n, edges, ws)
 
@@ -211,12 +215,13 @@ EDGE = _edge_graphs()
 
 @pytest.mark.parametrize("gname", list(EDGE))
 @pytest.mark.parametrize("form", ["nodp", "cdp", "tc", "tca", "mb", "block", "persist", "persist-nodp",
-                                  "tca-nosmall", "tca-small1", "tca-small33-cta", "tca-sweep"])
+                                  "tca-nosmall", "tca-small1", "tca-small1024", "tca-small33-cta", "tca-sweep"])
 def test_edge_graphs(ctx, gname, form):
     g = EDGE[gname]
     kw = {"mb": dict(granularity="multiblock", group_blocks=2, threshold=4),
           "tca-nosmall": dict(small_parents=0),
           "tca-small1": dict(small_parents=1, unroll=1),
+          "tca-small1024": dict(small_parents=1024),
           "tca-small33-cta": dict(small_parents=33, serial=npb.NP_SERIAL_BLOCK, unroll=3),
           "tca-sweep": dict(sweep_parents=1, small_parents=64),
           "block": dict(granularity="block", threshold=1, cfactor=2),
