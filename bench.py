@@ -17,7 +17,7 @@ Other workloads (--workload): bfs-rmat20 (BFS on the same graph), bfs4k (the
 4096-vertex power-law digraph), road (a 264K-vertex grid road graph with
 out-degree <= 8: the low-nested-parallelism case, with the never-taken launch
 site measured against the same kernel without it), bt64k (Bezier tessellation
-of 65,536 curves, points/s), tc-rmat17 (triangle counting on the simple
+of 65,536 curves, points/s; bt256k: 262,144 curves, whose points exceed L2), tc-rmat17 (triangle counting on the simple
 undirected R-MAT scale-17 graph: the second CSR workload, an adjacency-
 intersection child; oriented edges/s), batched-sssp / batched-bfs (512 R-MAT instances,
 n log-uniform in [2^10, 2^20], edge factor 8..32, in one CUDA graph launch
@@ -78,6 +78,11 @@ WORKLOADS = {
     "bt64k": dict(kind="bezier", graph=None,
                   config=dict(workload="bezier_tessellation_65536_curves", curves=65536,
                               points="ceil(sqrt(kappa)*64) clamped to [4,4096]", seed=3)),
+    # four times the curves: about 200 MB of points, more than L2, so the child grid's point
+    # stores reach DRAM within the timed kernel
+    "bt256k": dict(kind="bezier", graph=None,
+                   config=dict(workload="bezier_tessellation_262144_curves", curves=262144,
+                               points="ceil(sqrt(kappa)*64) clamped to [4,4096]", seed=3)),
 }
 
 
@@ -86,6 +91,7 @@ WORKLOADS = {
 TUNED = {# tessellation: 512-thread parent CTAs make the output-offset look-back groups 16 tiles long;
          # the curves below the threshold spread over the parent CTA (44.1 against 45.2 us)
          "bt64k": dict(parent_block=512, child_block=32, cfactor=4, serial=2),   # serial 2: NP_SERIAL_BLOCK
+         "bt256k": dict(parent_block=512, child_block=32, cfactor=4, serial=2),
          "tc-rmat17": dict(threshold=8, child_block=32, cfactor=1),
          # SSSP: every grid level's children only reduce and a sweep over the vertex state forms the
          # next frontier (A/B on GB300: 454 -> 436 us; BFS, whose claims rarely reach the atomic,
@@ -293,7 +299,7 @@ def run_reference(args, ws, rank):
         return run_reference_multi(args, ws, wl)
     if wl["kind"] == "bezier":
         from paper_2201_02789_gb300 import gen
-        ctrl = gen.bt64k()
+        ctrl = gen.bezier_curves(wl["config"]["curves"], seed=wl["config"]["seed"])
         run = lambda: oracle.bezier(ctrl)
         units = lambda out: int(out[0][-1])
         unit = "Gpoints/s"
@@ -444,22 +450,23 @@ class GraphWorkload:
 
 
 class BezierWorkload:
-    """Tessellation of the 64K-curve set through np_bezier."""
+    """Tessellation of a seeded curve set (65,536 curves by default) through np_bezier."""
 
-    def __init__(self, dev, stream, ctx):
+    def __init__(self, dev, stream, ctx, ncurves=65536, seed=3):
         import torch
         from paper_2201_02789_gb300 import gen
         from paper_2201_02789_gb300 import nestpar as npb
         self.npb, self.stream, self.ctx, self.kind = npb, stream, ctx, "bezier"
-        self.ctrl = gen.bt64k()
+        self.nc = ncurves
+        self.ctrl = gen.bezier_curves(ncurves, seed=seed)
         self.c_d = torch.from_numpy(self.ctrl).to(dev)
-        self.cap = 65536 * 200
-        self.off = torch.empty(65537, dtype=torch.int32, device=dev)
+        self.cap = ncurves * 200
+        self.off = torch.empty(ncurves + 1, dtype=torch.int32, device=dev)
         self.pts = torch.empty((self.cap, 2), dtype=torch.float32, device=dev)
         self.unit = "Gpoints/s"
 
     def solve(self, cfg, stats=False):
-        return self.npb.np_bezier(self.ctx.handle, self.c_d, 65536, self.off, self.pts, self.cap, cfg,
+        return self.npb.np_bezier(self.ctx.handle, self.c_d, self.nc, self.off, self.pts, self.cap, cfg,
                                   stream=self.stream, stats=stats)
 
     def result(self):
@@ -490,18 +497,18 @@ class BezierWorkload:
     def e2e(self, cfg, steps, flush, dev):
         import torch
         c_h = torch.from_numpy(self.ctrl).pin_memory()
-        off_h = torch.empty(65537, dtype=torch.int32).pin_memory()
+        off_h = torch.empty(self.nc + 1, dtype=torch.int32).pin_memory()
         pts_h = torch.empty((self.cap, 2), dtype=torch.float32).pin_memory()
         ms = []
         for k in range(steps + 1):
             flush.zero_()
             torch.cuda.synchronize(dev)
             t = time.perf_counter()
-            self.npb.np_bezier_host(self.ctx.handle, c_h, 65536, off_h, pts_h, self.cap, cfg, stream=self.stream)
+            self.npb.np_bezier_host(self.ctx.handle, c_h, self.nc, off_h, pts_h, self.cap, cfg, stream=self.stream)
             if k:
                 ms.append((time.perf_counter() - t) * 1e3)
         total = int(off_h[-1].item())
-        return ms, 24 * 65536, 4 * 65537 + 8 * total, off_h.numpy().copy()
+        return ms, 24 * self.nc, 4 * (self.nc + 1) + 8 * total, off_h.numpy().copy()
 
 
 class TcWorkload:
@@ -579,7 +586,7 @@ def comparison_forms(npb, workload: str, cdp_steps: int):
                 ("cdp_threshold_above_max_degree", npb.config("cdp", threshold=npb.INT32_MAX, **chunk), 5),
                 ("plain_cdp", npb.config("cdp"), cdp_steps),
                 ("t_c", npb.config("tc"), cdp_steps)]
-    graph_only = [] if workload in ("bt64k", "tc-rmat17") else [
+    graph_only = [] if workload in ("bt64k", "bt256k", "tc-rmat17") else [
         ("t_c_a_persistent", npb.config("tca", driver=npb.NP_DRIVER_PERSISTENT), 5),
         ("nodp_persistent", npb.config("nodp", driver=npb.NP_DRIVER_PERSISTENT), 5)]
     return [("plain_cdp", npb.config("cdp"), cdp_steps), ("nodp", npb.config("nodp"), cdp_steps),
@@ -606,7 +613,7 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 << 20, dtype=torch.int8, device=dev)
     if wl["kind"] == "bezier":
-        W = BezierWorkload(dev, stream, ctx)
+        W = BezierWorkload(dev, stream, ctx, wl["config"]["curves"], wl["config"]["seed"])
     elif wl["kind"] == "tc":
         W = TcWorkload(dev, stream, ctx)
     else:
@@ -697,8 +704,12 @@ def run_ours(args, ws, rank, local):
     npb.np_profile_enable(ctx.handle, False)
     kb = kernel_bytes(wl["kind"], pst, W)
     peak, peak_kind = hbm_peak()
-    kernels = {"child_agg": (prof["child_ms"], prof["child_launches"], kb["child"]),
-               "parent_warp": (prof["parent_ms"], prof["parent_launches"], kb["parent"])}
+    # the grid-host form's parent kernel: warp tiles, or CTA tiles for the CTA-spread / packed
+    # serial children (whose child grid is child_agg_pack)
+    cta = cfg.serial in (npb.NP_SERIAL_BLOCK, npb.NP_SERIAL_PACKED)
+    child_name = "child_agg_pack" if cfg.serial == npb.NP_SERIAL_PACKED else "child_agg"
+    kernels = {child_name: (prof["child_ms"], prof["child_launches"], kb["child"]),
+               ("parent_cta" if cta else "parent_warp"): (prof["parent_ms"], prof["parent_launches"], kb["parent"])}
     dom = max(kernels, key=lambda k: kernels[k][0])
     k_ms, k_launches, k_bytes = kernels[dom]
     per_launch_bytes = k_bytes * prof_runs / max(k_launches, 1)
@@ -1228,7 +1239,7 @@ def run_sweep(args, local, wl):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 << 20, dtype=torch.int8, device=dev)
     if wl["kind"] == "bezier":
-        W = BezierWorkload(dev, stream, ctx)
+        W = BezierWorkload(dev, stream, ctx, wl["config"]["curves"], wl["config"]["seed"])
     elif wl["kind"] == "tc":
         W = TcWorkload(dev, stream, ctx)
     else:

@@ -503,6 +503,19 @@ def test_bt64k_full(ctx):
     assert rel <= 16 * 2.0 ** -24 / 1e-3
 
 
+def test_bt256k_full(ctx):
+    """262,144 curves (about 25 M points, more than L2 holds) in the benchmark's setting:
+    offsets exact, points within the tolerance."""
+    import bench
+    ctrl = gen.bezier_curves(262144, seed=3)
+    ref_off, ref_pts = oracle.bezier(ctrl)
+    status, off, pts, st = bezier(ctx, ctrl, npb.config("tca", **bench.TUNED["bt256k"]), cap=int(ref_off[-1]))
+    assert status == npb.NP_OK and st["error"] == 0
+    np.testing.assert_array_equal(off, ref_off)
+    ok, worst = bezier_tolerance_ok(pts, ref_pts)
+    assert ok, worst
+
+
 def test_bench_tuned_configs_full(ctx, g4k):
     """The configurations bench.py times where they differ from the library default (BT-64K
     with 512-thread parent CTAs, 32-thread child blocks, CF 4 and the serial children spread
