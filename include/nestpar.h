@@ -150,7 +150,9 @@ typedef struct np_config {
 } np_config;
 
 /* Fills the library defaults: CDP, threshold 32, cfactor 4, grid-host
- * aggregation, atomic scan, child block 64, parent block 256, AUTO driver
+ * aggregation, atomic scan, child block 64, parent block 256, AUTO driver,
+ * serial children spread over the parent warp, the small-level loop for levels
+ * of up to 2048 parents, appended frontiers
  * (the best of a threshold x cfactor x child-block x scan sweep of BFS and SSSP
  * on an R-MAT scale-20 graph on GB300; the look-back scan, which keeps records
  * in parent order, is selectable and slower there because it publishes and
