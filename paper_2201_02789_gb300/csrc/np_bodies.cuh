@@ -22,6 +22,7 @@ struct BfsBody {
   static constexpr bool kBalance = false;   // child blocks cost the same: static ranges
   static constexpr int kStage = 1;          // edge lists the child can stage: col
   static constexpr int kWarpParentRegs = NP_WARP_PARENT_MAXREG;
+  static constexpr int kCtaParentRegs = NP_CTA_PARENT_MAXREG;
   struct P {
     int base;
     int qbase;   // query part of the ids of this parent's children
@@ -71,6 +72,7 @@ struct SsspBody {
   static constexpr bool kBalance = false;
   static constexpr int kStage = 2;          // col and w
   static constexpr int kWarpParentRegs = 96;   // (the stamp form spills at 80)
+  static constexpr int kCtaParentRegs = NP_CTA_PARENT_MAXREG;
   struct P {
     int base;
     unsigned du;
@@ -181,6 +183,7 @@ struct TcBody {
   static constexpr bool kBalance = true;    // block cost varies with the lists' lengths
   static constexpr int kStage = 0;
   static constexpr int kWarpParentRegs = NP_WARP_PARENT_MAXREG;
+  static constexpr int kCtaParentRegs = NP_CTA_PARENT_MAXREG;
   struct P {
     int base;
     int n;
@@ -246,6 +249,7 @@ struct Sssp64Body {
   static constexpr bool kBalance = false;
   static constexpr int kStage = 2;          // col and w
   static constexpr int kWarpParentRegs = NP_WARP_PARENT_MAXREG;
+  static constexpr int kCtaParentRegs = NP_CTA_PARENT_MAXREG;
   struct P {
     int base;
     unsigned du;
@@ -375,11 +379,14 @@ struct BezierBody {
   static constexpr bool kPushes = false;
   static constexpr bool kBalance = false;
   static constexpr int kStage = 0;
-  static constexpr int kWarpParentRegs = 128;   // (32-byte parents: no cap below that without spills)
+  static constexpr int kWarpParentRegs = 128;   // (36-byte parents: no cap below that without spills)
+  // (64 still fits two 512-thread CTAs per SM, as 48 does; 48 spills)
+  static constexpr int kCtaParentRegs = 64;
   struct P {
     float x0, y0, x1, y1, x2, y2;
     int base;
-    float denom;
+    float inv;   // 1 / (N - 1), correctly rounded
+    float nm1;   // N - 1 (exact)
   };
   struct F {};
   // Point count in FP64 with correctly rounded operations only, so that it is
@@ -444,8 +451,8 @@ struct BezierBody {
   }
   __device__ static P parent(const BodyArgs& b, int pid, int base, int N) {
     const float* c = b.ctrl + 6 * (size_t)pid;
-    return P{__ldg(c), __ldg(c + 1), __ldg(c + 2), __ldg(c + 3), __ldg(c + 4), __ldg(c + 5), base,
-             (float)(N - 1)};
+    const float nm1 = (float)(N - 1);
+    return P{__ldg(c), __ldg(c + 1), __ldg(c + 2), __ldg(c + 3), __ldg(c + 4), __ldg(c + 5), base, 1.0f / nm1, nm1};
   }
   __device__ static unsigned aux(const BodyArgs&, int) { return 0u; }
   __device__ static P parent_aux(const BodyArgs& b, int pid, int base, int N, unsigned) {
@@ -454,7 +461,7 @@ struct BezierBody {
   __device__ static P shfl(const P& p, int src) {
     return P{__shfl_sync(kFull, p.x0, src), __shfl_sync(kFull, p.y0, src), __shfl_sync(kFull, p.x1, src),
              __shfl_sync(kFull, p.y1, src), __shfl_sync(kFull, p.x2, src), __shfl_sync(kFull, p.y2, src),
-             __shfl_sync(kFull, p.base, src), __shfl_sync(kFull, p.denom, src)};
+             __shfl_sync(kFull, p.base, src), __shfl_sync(kFull, p.inv, src), __shfl_sync(kFull, p.nm1, src)};
   }
   __device__ static F fetch(const BodyArgs&, const P&, int) { return F{}; }
   template <int K>
@@ -465,9 +472,13 @@ struct BezierBody {
       push[k] = false;
       v[k] = 0;
       if (!valid[k]) continue;
+      // t = j / (N - 1) and u = 1 - t = (N - 1 - j) / (N - 1), each from the
+      // exact integer numerator times the parent's reciprocal: no division per
+      // point, and u keeps its relative accuracy near t = 1, where 1 - t would
+      // cancel
       const P& q = p[k];
-      const float t = (float)idx[k] / q.denom;
-      const float u = 1.0f - t;
+      const float t = (float)idx[k] * q.inv;
+      const float u = (q.nm1 - (float)idx[k]) * q.inv;
       const float b0 = u * u, b1 = 2.0f * u * t, b2 = t * t;
       b.points[q.base + idx[k]] =
           make_float2(b0 * q.x0 + b1 * q.x1 + b2 * q.x2, b0 * q.y0 + b1 * q.y1 + b2 * q.y2);

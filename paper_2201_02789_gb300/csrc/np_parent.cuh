@@ -499,15 +499,13 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
 //     a.pack == 1  they go packed to the child grid: prec = {parent, start, N,
 //                  first item} and pfirst[k] = that record when it holds item
 //                  k * kPackItems (N < kPackItems: at most one chunk start).
-// Capped at 48 registers: five 256-thread CTAs per SM.
-#ifndef NP_CTA_PARENT_MAXREG
-#define NP_CTA_PARENT_MAXREG 48
-#endif
+// Capped at Body::kCtaParentRegs registers (48 for the graph bodies: five
+// 256-thread CTAs per SM).
 #ifndef NP_CTA_SPREAD_BATCH
 #define NP_CTA_SPREAD_BATCH 4
 #endif
 template <class Body>
-__global__ void __maxnreg__(NP_CTA_PARENT_MAXREG) parent_cta(Args a) {
+__global__ void __maxnreg__(Body::kCtaParentRegs) parent_cta(Args a) {
   NP_PDL_ENTRY();
   // items per thread per round of the CTA-wide serial loop (the tessellation's
   // 32-byte parent takes two)

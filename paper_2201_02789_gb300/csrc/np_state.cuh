@@ -80,6 +80,11 @@
 #ifndef NP_WARP_PARENT_MAXREG
 #define NP_WARP_PARENT_MAXREG 80
 #endif
+// Register cap of the CTA-tiled grid-host parent: 48, five 256-thread CTAs per
+// SM (the tessellation's 36-byte parents take 64, kCtaParentRegs).
+#ifndef NP_CTA_PARENT_MAXREG
+#define NP_CTA_PARENT_MAXREG 48
+#endif
 
 namespace nestpar {
 
