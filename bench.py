@@ -88,15 +88,21 @@ WORKLOADS = {
 
 # per-workload values of the aggregated form's knobs, from threshold x cfactor x child-block
 # sweeps on GB300 (the paper also tunes T and CF per benchmark); other workloads use the defaults
-TUNED = {# tessellation: 512-thread parent CTAs make the output-offset look-back groups 16 tiles long;
-         # the curves below the threshold spread over the parent CTA (44.1 against 45.2 us)
-         "bt64k": dict(parent_block=512, child_block=32, cfactor=4, serial=2),   # serial 2: NP_SERIAL_BLOCK
-         "bt256k": dict(parent_block=512, child_block=32, cfactor=4, serial=2),
+TUNED = {# tessellation: a threshold above every count, so that each curve's points run in its parent
+         # warp (a whole warp per curve of 32 points or more) and no child grid is launched: 35 against
+         # 42 us with the aggregated child grid below (BT_CHILD_GRID); 512-thread parent CTAs make the
+         # output-offset look-back groups 16 tiles long
+         "bt64k": dict(threshold=2**31 - 1, parent_block=512),
+         "bt256k": dict(threshold=2**31 - 1, parent_block=512),
          "tc-rmat17": dict(threshold=8, child_block=32, cfactor=1),
          # SSSP: every grid level's children only reduce and a sweep over the vertex state forms the
          # next frontier (A/B on GB300: 454 -> 436 us; BFS, whose claims rarely reach the atomic,
          # loses 181 -> 187 us and keeps the appending frontier)
          "sssp-rmat20": dict(sweep_parents=1)}
+# the tessellation's best form with an aggregated child grid: T 32 (the default), 32-thread child
+# blocks of 4 original blocks, 512-thread parent CTAs spreading the serialised points over the CTA
+# (serial 2: NP_SERIAL_BLOCK); timed beside the headline
+BT_CHILD_GRID = dict(parent_block=512, child_block=32, cfactor=4, serial=2)
 # (the 4096-vertex graph, latency-bound, runs almost every level in the while driver's one-CTA
 # small-level loop: 115 us, against 150 us on the persistent level loop with 8 CTAs)
 
@@ -592,6 +598,8 @@ def comparison_forms(npb, workload: str, cdp_steps: int):
                 ("cdp_threshold_above_max_degree", npb.config("cdp", threshold=npb.INT32_MAX, **chunk), 5),
                 ("plain_cdp", npb.config("cdp"), cdp_steps),
                 ("t_c", npb.config("tc"), cdp_steps)]
+    bt_only = [("t_c_a_grid_host_child_grid", npb.config("tca", **BT_CHILD_GRID), 20)] \
+        if workload in ("bt64k", "bt256k") else []
     graph_only = [] if workload in ("bt64k", "bt256k", "tc-rmat17") else [
         ("t_c_a_persistent", npb.config("tca", driver=npb.NP_DRIVER_PERSISTENT), 5),
         ("nodp_persistent", npb.config("nodp", driver=npb.NP_DRIVER_PERSISTENT), 5)]
@@ -599,7 +607,7 @@ def comparison_forms(npb, workload: str, cdp_steps: int):
             ("t_c", npb.config("tc"), cdp_steps),
             ("t_c_a_multiblock", npb.config("tca", granularity="multiblock", group_blocks=8), 5),
             ("t_c_a_grid_device", npb.config("tca", granularity="grid_device"), 5),
-            ("t_c_a_block", npb.config("tca", granularity="block"), 5)] + graph_only
+            ("t_c_a_block", npb.config("tca", granularity="block"), 5)] + bt_only + graph_only
 
 
 def run_ours(args, ws, rank, local):
@@ -659,8 +667,9 @@ def run_ours(args, ws, rank, local):
     # kernels launched per solve: graph solves launch init (+ the small-level loop once before
     # the while loop) + per while-body iteration `unroll` x (parent, child[, sweep]) + the
     # condition kernel (the small-level loop); a tessellation launches init, parent and child
+    # (no child when the threshold launches nothing and no children are packed for it)
     if wl["kind"] == "bezier":
-        per_solve = 3
+        per_solve = 2 if cfg.threshold == npb.INT32_MAX and cfg.serial != npb.NP_SERIAL_PACKED else 3
     elif wl["kind"] == "tc":
         per_solve = 4          # level-state reset, parent, child, partial-count sum
     else:
@@ -784,8 +793,11 @@ def run_ours(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"bezier": "f32", "tc": "i32"}.get(wl["kind"], "u32"), "data": "synthetic",
             "config": dict(wl["config"], l2=L2_NOTE),
-            "form": f"threshold {cfg.threshold} + coarsening {cfg.cfactor} ({cfg.child_block}-thread child blocks) "
-                    "+ grid aggregation (atomic scan), " + (
+            "form": ("threshold INT32_MAX (no child launches: the serialised children run in the parent "
+                     "warps, a whole warp per parent of 32 or more), " if cfg.threshold == npb.INT32_MAX else
+                     f"threshold {cfg.threshold} + coarsening {cfg.cfactor} ({cfg.child_block}-thread child blocks) "
+                     "+ grid aggregation (atomic scan), ") + (
+                        "one fixed pass replayed as a CUDA graph" if wl["kind"] in ("bezier", "tc") else
                         f"persistent cooperative level loop on {cfg.parent_grid} CTAs"
                         if cfg.driver == npb.NP_DRIVER_PERSISTENT else "while-graph level loop"),
             "ms_per_solve": {"median": statistics.median(ms), "min": min(ms)},

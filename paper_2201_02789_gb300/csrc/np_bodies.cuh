@@ -21,6 +21,7 @@ struct BfsBody {
   static constexpr bool kPushes = true;
   static constexpr bool kBalance = false;   // child blocks cost the same: static ranges
   static constexpr int kStage = 1;          // edge lists the child can stage: col
+  static constexpr bool kWarpLoop = false;
   static constexpr int kWarpParentRegs = NP_WARP_PARENT_MAXREG;
   static constexpr int kCtaParentRegs = NP_CTA_PARENT_MAXREG;
   struct P {
@@ -71,6 +72,7 @@ struct SsspBody {
   static constexpr bool kPushes = true;
   static constexpr bool kBalance = false;
   static constexpr int kStage = 2;          // col and w
+  static constexpr bool kWarpLoop = false;
   static constexpr int kWarpParentRegs = 96;   // (the stamp form spills at 80)
   static constexpr int kCtaParentRegs = NP_CTA_PARENT_MAXREG;
   struct P {
@@ -182,6 +184,7 @@ struct TcBody {
   static constexpr bool kPushes = false;
   static constexpr bool kBalance = true;    // block cost varies with the lists' lengths
   static constexpr int kStage = 0;
+  static constexpr bool kWarpLoop = false;
   static constexpr int kWarpParentRegs = NP_WARP_PARENT_MAXREG;
   static constexpr int kCtaParentRegs = NP_CTA_PARENT_MAXREG;
   struct P {
@@ -248,6 +251,7 @@ struct Sssp64Body {
   static constexpr bool kPushes = true;
   static constexpr bool kBalance = false;
   static constexpr int kStage = 2;          // col and w
+  static constexpr bool kWarpLoop = false;
   static constexpr int kWarpParentRegs = NP_WARP_PARENT_MAXREG;
   static constexpr int kCtaParentRegs = NP_CTA_PARENT_MAXREG;
   struct P {
@@ -379,6 +383,9 @@ struct BezierBody {
   static constexpr bool kPushes = false;
   static constexpr bool kBalance = false;
   static constexpr int kStage = 0;
+  // serialised curves of 32 points or more run with the whole parent warp (a
+  // point only stores: one parent at a time beats spreading several)
+  static constexpr bool kWarpLoop = true;
   static constexpr int kWarpParentRegs = 128;   // (36-byte parents: no cap below that without spills)
   // (64 still fits two 512-thread CTAs per SM, as 48 does; 48 spills)
   static constexpr int kCtaParentRegs = 64;

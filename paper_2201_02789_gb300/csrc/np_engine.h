@@ -53,6 +53,9 @@ struct Plan {
   const void* loop = nullptr;   // persistent level loop (NODP and grid-host forms)
   const void* small = nullptr;  // one-CTA small-level loop before the while loop and at each body's end (grid-host)
   const void* sweep = nullptr;  // swept frontier: the kernel that rebuilds the next frontier after each level
+  // grid-host form that can give its child grid no work (threshold INT32_MAX,
+  // serialised children in the parent kernel): a fixed pass launches no child
+  bool child_idle = false;
   int mode = M_NODP;
   int gran = G_NODP;
 };

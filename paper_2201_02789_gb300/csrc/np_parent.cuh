@@ -85,7 +85,9 @@ __global__ void NP_PARENT_BOUNDS parent_kernel(Args a) {
   const int ntiles = ceil_div(count, PB);
   // CTAs beyond the number of tiles have nothing to take: leave at once
   if ((int)blockIdx.x >= ntiles) return;
+  // (INT32_MAX launches nothing, whatever N)
   const int T = a.threshold < 1 ? 1 : a.threshold;
+  const bool never = a.threshold == INT_MAX;
   const int CB = a.child_block;
   if (tid < S_N) s_stat[tid] = 0;
   CtaSink sink{b.next, b.next_count, s_q, &s_qn};
@@ -124,7 +126,7 @@ __global__ void NP_PARENT_BOUNDS parent_kernel(Args a) {
         N = 0;
       }
     }
-    const bool launch = GRAN != G_NODP && valid && N >= T;
+    const bool launch = GRAN != G_NODP && valid && !never && N >= T;
     const bool serial = valid && !launch && N > 0;
     warp_stat(s_stat, S_PARENTS, valid ? 1u : 0u);
     warp_stat(s_stat, S_ITEMS, (unsigned)N);
@@ -272,7 +274,9 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
   b.next = fixed ? a.next_ovr : ((L & 1) ? a.fr0 : a.fr1);
   b.next_count = fixed ? a.next_count_ovr : &st->count[(L + 1) % 3];
   b.sweep = !fixed && a.sweep_parents > 0 && count >= a.sweep_parents;
+  // (INT32_MAX launches nothing, whatever N)
   const int T = a.threshold < 1 ? 1 : a.threshold;
+  const bool never = a.threshold == INT_MAX;
   const int CB = a.child_block;
   StageSink sink{b.next, b.next_count, s_stage, s_stage_n};
 
@@ -348,7 +352,7 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
       }
       if (tile >= ntiles) continue;   // past the level's last tile: only the scan above needed this warp
     }
-    const bool launch = FORM == 1 && valid && N >= T;
+    const bool launch = FORM == 1 && valid && !never && N >= T;
     const bool serial = valid && !launch && N > 0;
     {
       const unsigned c_par = __popc(__ballot_sync(kFull, valid)), c_items = __reduce_add_sync(kFull, (unsigned)N);
@@ -396,14 +400,39 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
         st->agg_blocks[slot] = (int)(x.b + tb);
       }
     }
-    const int myN = serial ? N : 0;
     if constexpr (FORM == 1) {
-      // Serialised children of the aggregated form, spread over the warp's
-      // lanes: the tile's below-threshold children are numbered in parent
-      // order, item t goes to lane t % 32, which finds its parent (the first
-      // lane whose inclusive count exceeds t) by a shuffle search and takes
-      // the parent's fields by shuffle. The work stays in the parent kernel,
-      // with every lane busy instead of each lane walking only its own list.
+      // Serialised children of the aggregated form. The work stays in the
+      // parent kernel, with every lane busy instead of each lane walking only
+      // its own list.
+      if (__ballot_sync(kFull, serial) == 0u) continue;   // (uniform) no serialised children in this tile
+      const typename Body::P pm = Body::parent(b, serial ? pid : 0, base, N);
+      // Bodies with kWarpLoop: a parent with at least 32 serialised children
+      // runs them with the whole warp, one parent at a time: child j on lane
+      // j % 32, coalesced, the parent's fields taken by shuffle once.
+      const int wideN = Body::kWarpLoop && serial && N >= 32 ? N : 0;
+      const int myN = serial && wideN == 0 ? N : 0;
+      if constexpr (Body::kWarpLoop) {
+        for (unsigned wm = __ballot_sync(kFull, wideN > 0); wm; wm &= wm - 1) {
+          const int src = __ffs(wm) - 1;
+          const int n = __shfl_sync(kFull, wideN, src);
+          const typename Body::P p = Body::shfl(pm, src);
+          for (int j0 = 0; j0 < n; j0 += 32) {
+            typename Body::F f[1];
+            typename Body::P pk[1] = {p};
+            bool v[1] = {j0 + lane < n};
+            int idx[1] = {j0 + lane};
+            f[0] = v[0] ? Body::fetch(b, p, idx[0]) : typename Body::F{};
+            bool pf[1];
+            int pv[1];
+            Body::template apply_batch<1>(b, pk, idx, f, v, pf, pv);
+            if constexpr (Body::kPushes) sink.template push<1>(pf, pv);
+          }
+        }
+      }
+      // The others are spread over the warp's lanes: their children are
+      // numbered in parent order, item t goes to lane t % 32, which finds its
+      // parent (the first lane whose inclusive count exceeds t) by a shuffle
+      // search and takes the parent's fields by shuffle.
       int incl = myN;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -413,7 +442,6 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
       const int total = __shfl_sync(kFull, incl, 31);
       if (total > 0) {
         constexpr int KS = NP_SPREAD_BATCH;
-        const typename Body::P pm = Body::parent(b, serial ? pid : 0, base, N);
         const int excl = incl - myN;
         for (int t0 = 0; t0 < total; t0 += 32 * KS) {
           typename Body::F f[KS];
@@ -444,6 +472,7 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
     } else {
       // No-CDP form (the paper's baseline): lane l walks its own parent's
       // children in order; lanes with fewer (or none) idle through the tail
+      const int myN = serial ? N : 0;
       const int maxN = (int)__reduce_max_sync(kFull, (unsigned)myN);
       if (maxN > 0) {
         constexpr int KS = NP_SERIAL_BATCH;
@@ -534,7 +563,9 @@ __global__ void __maxnreg__(Body::kCtaParentRegs) parent_cta(Args a) {
   b.L = L;
   b.next = fixed ? a.next_ovr : ((L & 1) ? a.fr0 : a.fr1);
   b.next_count = fixed ? a.next_count_ovr : &st->count[(L + 1) % 3];
+  // (INT32_MAX launches nothing, whatever N)
   const int T = a.threshold < 1 ? 1 : a.threshold;
+  const bool never = a.threshold == INT_MAX;
   const int CB = a.child_block;
   if (tid == 0) s_stage_n = 0;
   StageSink sink{b.next, b.next_count, s_stage, &s_stage_n};
@@ -579,7 +610,7 @@ __global__ void __maxnreg__(Body::kCtaParentRegs) parent_cta(Args a) {
         N = 0;
       }
     }
-    const bool launch = valid && N >= T;
+    const bool launch = valid && !never && N >= T;
     const bool small = valid && !launch && N > 0;
     const unsigned cg = launch ? (unsigned)ceil_div(ceil_div(N, CB), a.cfactor) : 0u;
     uint4 ex, tot;

@@ -283,7 +283,13 @@ BT_FORMS = [("nodp", {}), ("cdp", {}), ("t", {}), ("tc", {}), ("tca", {}),
             ("tca", dict(serial=npb.NP_SERIAL_PACKED, threshold=200, child_block=1024, cfactor=1)),
             ("tca", dict(serial=npb.NP_SERIAL_BLOCK, threshold=64)),
             ("tca", dict(serial=npb.NP_SERIAL_BLOCK, threshold=npb.INT32_MAX, parent_block=64,
-                         scan=npb.NP_SCAN_LOOKBACK))]
+                         scan=npb.NP_SCAN_LOOKBACK)),
+            # serialised curves of 32 points or more run with the whole parent warp, the rest spread
+            # over its lanes: every curve in the parent warps, or all three kinds in one pass
+            ("tca", dict(threshold=npb.INT32_MAX, parent_block=512)),
+            ("tca", dict(threshold=npb.INT32_MAX, parent_block=64, scan=npb.NP_SCAN_LOOKBACK)),
+            ("tca", dict(threshold=40, child_block=32)),
+            ("tca", dict(threshold=1024, cfactor=2))]
 
 
 @pytest.mark.parametrize("form,kw", BT_FORMS, ids=[f"{f}-{i}" for i, (f, _) in enumerate(BT_FORMS)])
@@ -296,6 +302,36 @@ def test_bezier_forms(ctx, form, kw):
     ok, worst = bezier_tolerance_ok(pts[: ref_off[-1]], ref_pts)
     assert ok, worst
     assert st["items"] == ref_off[-1] and st["parents"] == 3000
+
+
+def _curves_around_a_warp():
+    """Curves with exactly 31, 32 and 33 points and the longest of a large random draw,
+    interleaved, so that a warp tile holds some of each."""
+    pool = gen.bezier_curves(40000, seed=35)
+    n = np.diff(oracle.bezier_offsets(pool))
+    pick = [np.flatnonzero(n == k)[:40] for k in (31, 32, 33)] + [np.argsort(n)[-40:]]
+    idx = np.stack([p[:min(len(q) for q in pick)] for p in pick], 1).reshape(-1)
+    return np.ascontiguousarray(pool[idx]), n[idx]
+
+
+@pytest.mark.parametrize("kw", [dict(threshold=npb.INT32_MAX), dict(threshold=33), dict(threshold=32),
+                                dict(threshold=npb.INT32_MAX, parent_block=512, scan=npb.NP_SCAN_LOOKBACK)],
+                         ids=["never", "T33", "T32", "never-pb512-lookback"])
+def test_bezier_whole_warp_curves(ctx, kw):
+    ctrl, counts = _curves_around_a_warp()
+    assert {31, 32, 33} <= set(counts.tolist()) and counts.max() > 1000
+    ref_off, ref_pts = oracle.bezier(ctrl)
+    status, off, pts, st = bezier(ctx, ctrl, npb.config("tca", **kw))
+    assert status == npb.NP_OK and st["error"] == 0
+    np.testing.assert_array_equal(off, ref_off)
+    ok, worst = bezier_tolerance_ok(pts[: ref_off[-1]], ref_pts)
+    assert ok, worst
+    assert st["items"] == ref_off[-1]
+    launching = int((counts >= kw["threshold"]).sum()) if kw["threshold"] != npb.INT32_MAX else 0
+    assert st["launch_parents"] == launching and st["serial_parents"] == len(counts) - launching
+    if launching == 0:
+        # a threshold that launches nothing: no child grid runs at all
+        assert st["child_blocks"] == 0 and st["child_items"] == 0
 
 
 @pytest.mark.parametrize("pb", [64, 128, 512])
