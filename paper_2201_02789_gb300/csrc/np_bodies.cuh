@@ -386,7 +386,7 @@ struct BezierBody {
   // serialised curves of 32 points or more run with the whole parent warp (a
   // point only stores: one parent at a time beats spreading several)
   static constexpr bool kWarpLoop = true;
-  static constexpr int kWarpParentRegs = 128;   // (36-byte parents: no cap below that without spills)
+  static constexpr int kWarpParentRegs = 64;   // (no spill: two 512-thread CTAs per SM)
   // (64 still fits two 512-thread CTAs per SM, as 48 does; 48 spills)
   static constexpr int kCtaParentRegs = 64;
   struct P {

@@ -441,7 +441,8 @@ __device__ __forceinline__ void parent_warp_run(const Args& a, int L, int count,
       }
       const int total = __shfl_sync(kFull, incl, 31);
       if (total > 0) {
-        constexpr int KS = NP_SPREAD_BATCH;
+        // (the tessellation's 36-byte parents take two items per lane)
+        constexpr int KS = sizeof(typename Body::P) > 16 ? 2 : NP_SPREAD_BATCH;
         const int excl = incl - myN;
         for (int t0 = 0; t0 < total; t0 += 32 * KS) {
           typename Body::F f[KS];
