@@ -105,7 +105,9 @@ namespace nestpar {
 // thread takes two consecutive parents (count, row bounds), a CTA scan gives the
 // items' offsets, the parents are staged in shared memory, and the CTA's threads take
 // the items, each finding its parent by a binary search over the staged
-// offsets; CTA barriers separate the levels. It keeps the level state as the
+// offsets; CTA barriers separate the levels. A level whose appends all fit
+// the CTA's stage hands them to the next level in shared memory (and to the
+// global frontier with plain stores). It keeps the level state as the
 // parent and child grids do (slots and the count two levels ahead cleared,
 // counts rotated), so the grids continue from the level where it stops: the
 // first one too large, or an empty frontier. It runs once before the loop and
@@ -136,19 +138,24 @@ __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditional
   const int L0 = __ldcg(&st->base) + K;
   int L = L0;
   unsigned long long n_par = 0, n_items = 0, n_serial = 0;
+  // The level's frontier: from global memory at the first level; after a level
+  // of this loop whose appends all fit the stage, from the stage itself (the
+  // level's count in `staged`, -1 otherwise), so the next level starts without
+  // a round trip for its count and ids.
+  int staged = -1;
   for (;;) {
     // written before this kernel or by this CTA before the last barrier: the
     // same value in every thread
-    const int count = __ldcg(&st->count[L % 3]);
+    const int count = staged >= 0 ? staged : __ldcg(&st->count[L % 3]);
     if (count <= 0 || count > limit || L >= max_levels) break;
-    const int* ids = (L & 1) ? a.fr1 : a.fr0;
+    const int* ids = staged >= 0 ? s_stage : ((L & 1) ? a.fr1 : a.fr0);
     int pid[PPT], base[PPT], N[PPT];
     bool valid[PPT];
     unsigned mine = 0;
 #pragma unroll
     for (int r = 0; r < PPT; r++) {
       const int i = PPT * tid + r;
-      pid[r] = i < count ? __ldcg(&ids[i]) : 0;
+      pid[r] = i < count ? (staged >= 0 ? ids[i] : __ldcg(&ids[i])) : 0;
       valid[r] = i < count && pid[r] >= 0;
       base[r] = 0;
       N[r] = 0;
@@ -209,7 +216,24 @@ __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditional
       if constexpr (Body::kPushes) sink.template push<KS>(pf, pv);
     }
     // appends reach the next frontier and its count before the next level reads them
-    if constexpr (Body::kPushes) stage_flush(s_stage, &s_stage_n, b.next, b.next_count, &s_stage_base);
+    if constexpr (Body::kPushes) {
+      __syncthreads();
+      const int total = s_stage_n;   // the level's appends, the ones beyond the stage included
+      if (total <= kCtaStage) {
+        // all in the stage: this CTA made every append to the next frontier,
+        // so plain stores place them (for the grids, should they take over)
+        // and the next level reads them from the stage
+        for (int i = tid; i < total; i += nt) b.next[i] = s_stage[i];
+        if (tid == 0) *b.next_count = total;
+        staged = total;
+      } else {
+        // the stage overflowed (those appends reserved their slots at once):
+        // reserve the stage's part and copy it out; the next level is too
+        // large for this loop
+        stage_flush(s_stage, &s_stage_n, b.next, b.next_count, &s_stage_base);
+        staged = -1;
+      }
+    }
 #pragma unroll
     for (int r = 0; r < PPT; r++) {
       n_par += valid[r] ? 1u : 0u;
