@@ -1082,6 +1082,7 @@ def run_batched(args, ws, rank, local, wl):
                          "threshold": c["config"]["threshold"], "cfactor": c["config"]["cfactor"],
                          "child_block": c["config"]["child_block"],
                          "form": "nodp" if c["config"]["variant"] == 0 else "grid_host_aggregation",
+                         "swept_frontier": c["config"]["sweep_parents"] > 0,
                          # the best device-launch granularity, timed outside the graph (not pickable)
                          "device_launch_ms": c["device_launch_ms"],
                          "device_launch_form": {2: "block", 3: "multiblock8", 4: "grid_device"}.get(

@@ -113,9 +113,9 @@ typedef int32_t np_status;
 /* How a level loop forms the next frontier. By default children append each
  * vertex they reach (the relaxation's or claim's atomic returns the old value
  * to decide it; one atomic per warp batch reserves the places). With
- * sweep_parents > 0 (np_bfs / np_sssp, grid-host aggregation with
- * NP_SERIAL_SPREAD, graph / chunk / host driver), a level with at least that
- * many parents instead has its children only reduce (a fire-and-forget atomic
+ * sweep_parents > 0 (np_bfs / np_sssp and the classes of a batch; grid-host
+ * aggregation with NP_SERIAL_SPREAD, graph / chunk / host driver), a level with
+ * at least that many parents instead has its children only reduce (a fire-and-forget atomic
  * min of the level, or of the packed distance and tag), and a sweep over the
  * vertex state after the level collects the vertices it reached, in vertex
  * order. Other calls and forms append. */
@@ -144,7 +144,7 @@ typedef struct np_config {
                             of each body one CTA runs whole levels itself while the frontier
                             has at most this many parents (<= NP_SMALL_PARENTS_MAX) and at
                             most 16384 children in all; 0 = off */
-  int32_t sweep_parents; /* np_bfs / np_sssp: levels with at least this many parents form the
+  int32_t sweep_parents; /* np_bfs / np_sssp / batch classes: levels with at least this many parents form the
                             next frontier by a sweep (see below); 0 = every level appends */
   int32_t reserved[1];   /* must be zero */
 } np_config;
@@ -295,7 +295,8 @@ np_status np_batch_set_config(np_batch *b, int32_t cls, const np_config *cfg);
  * each class, runs the class's groups alone under each candidate configuration
  * (no dynamic parallelism; grid-host aggregation with threshold T in {8, 32,
  * 128, 512}, coarsening factor in {2, 8} and child block in {32, 128}), `reps`
- * times each (0 = 3), and keeps the configuration with the least minimum time.
+ * times each (0 = 3), and keeps the configuration with the least minimum time;
+ * then the kept one with a swept frontier (sweep_parents 1), kept if faster.
  * It also times the device-launch granularities (see np_batch_class), which
  * it reports but cannot pick. `out` (device, total elements) is overwritten. */
 np_status np_batch_tune(np_batch *b, void *out, int32_t reps, void *stream);

@@ -114,6 +114,7 @@ void group_args(np_batch* b, Group& g, const np_config& cfg, void* out, Args& a)
   a.b.dist = b->kind == 1 ? reinterpret_cast<unsigned*>(out) + g.vbase : nullptr;
   a.b.stamp = wsp<int>(g.ws, g.ws.lay.off_stamp);
   a.b.dtag = g.dtag;
+  a.n_vertices = g.n;   // (a swept frontier sweeps the group's union)
 }
 
 // fill + seed for one group on stream s (used by the tuner)
@@ -322,7 +323,6 @@ np_status np_batch_create(np_ctx* ctx, int32_t count, const np_csr* graphs, cons
     Class c;
     c.log2_lo = k;
     c.cfg = opt->config;
-    c.cfg.sweep_parents = 0;   // (the frontier sweep covers single solves)
     const int ci = (int)b->classes.size();
     Group* cur = nullptr;
     for (int i = 0; i < count; i++) {
@@ -456,7 +456,6 @@ np_status np_batch_set_config(np_batch* b, int32_t cls, const np_config* cfg) {
   if (!batch_form_ok(*cfg)) return NP_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lk(b->mu);
   b->classes[(size_t)cls].cfg = *cfg;
-  b->classes[(size_t)cls].cfg.sweep_parents = 0;
   b->classes[(size_t)cls].tuned_ms = 0.0;
   drop_batch_graph(b);
   return NP_OK;
@@ -500,9 +499,24 @@ np_status np_batch_tune(np_batch* b, void* out, int32_t reps, void* stream) {
         pick = c;
       }
     }
+    // the pick with a swept frontier (every grid level's children only reduce,
+    // a sweep over the group's vertex state forms the next frontier)
+    int timed = (int)cands.size();
+    np_config x = pick;
+    x.sweep_parents = 1;
+    if (pick.sweep_parents != 1 && sweeps(x)) {
+      double ms = 0.0;
+      NP_TRY(time_class(b, (int)ci, x, out, 1, s, &ms));
+      NP_TRY(time_class(b, (int)ci, x, out, reps, s, &ms));
+      timed++;
+      if (ms < best) {
+        best = ms;
+        pick = x;
+      }
+    }
     b->classes[ci].cfg = pick;
     b->classes[ci].tuned_ms = best;
-    b->classes[ci].candidates = (int)cands.size();
+    b->classes[ci].candidates = timed;
     // the device-launch granularities, for the record (Section VII-C's third axis)
     double dl_best = 1e30;
     for (int gran : {NP_GRAN_BLOCK, NP_GRAN_MULTIBLOCK, NP_GRAN_GRID_DEVICE})

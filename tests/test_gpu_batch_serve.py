@@ -97,10 +97,13 @@ def _check_batch(graphs, srcs, out_h, offs, kind, sample=None):
 
 
 @pytest.mark.parametrize("kind", [npb.NP_BATCH_BFS, npb.NP_BATCH_SSSP])
-@pytest.mark.parametrize("form", ["tca", "nodp", "tca-T1"])
+@pytest.mark.parametrize("form", ["tca", "nodp", "tca-T1", "tca-sweep", "tca-sweep-mixed"])
 def test_batch_matches_oracle(ctx, kind, form):
+    # (swept frontier: every grid level, or only levels of at least 50 parents)
     cfg = {"tca": npb.config("tca"), "nodp": npb.config("nodp"),
-           "tca-T1": npb.config("tca", threshold=1, cfactor=2, child_block=64)}[form]
+           "tca-T1": npb.config("tca", threshold=1, cfactor=2, child_block=64),
+           "tca-sweep": npb.config("tca", sweep_parents=1, small_parents=0),
+           "tca-sweep-mixed": npb.config("tca", sweep_parents=50)}[form]
     specs, graphs, srcs, devs = _batch_inputs(48, 6.0, 14.0, 40 + kind, kind)
     # small groups: several groups per class, and classes of width 2
     b = npb.np_batch_create(ctx.handle, [d.csr for d in devs], srcs, kind, cfg, max_group_edges=40000)
@@ -135,9 +138,11 @@ def test_batch_tune_then_run(ctx):
         npb.np_batch_tune(b, out, reps=2)
         classes = npb.np_batch_classes(b)
         for c in classes:
-            assert c["tuned_ms"] > 0 and c["candidates"] == 17
+            # 17 candidates, and the pick with a swept frontier when its form can sweep
+            assert c["tuned_ms"] > 0 and c["candidates"] in (17, 18)
             cfg = c["config"]
             assert cfg["variant"] == npb.NP_VARIANT_NODP or cfg["granularity"] == npb.NP_GRAN_GRID_HOST
+            assert cfg["sweep_parents"] in (0, 1)
         out.fill_(3)
         _, st = npb.np_batch_run(b, out, stats=True)
         assert st["error"] == 0
@@ -146,6 +151,10 @@ def test_batch_tune_then_run(ctx):
         s = npb.np_batch_set_config(b, 0, npb.config("cdp"), check=False)
         assert s == npb.NP_ERR_UNSUPPORTED
         npb.np_batch_set_config(b, 0, npb.config("tca", threshold=64))
+        npb.np_batch_run(b, out)
+        _check_batch(graphs, srcs, out.cpu().numpy().view(np.uint32), offs, kind)
+        npb.np_batch_set_config(b, 0, npb.config("tca", sweep_parents=1))
+        out.fill_(3)
         npb.np_batch_run(b, out)
         _check_batch(graphs, srcs, out.cpu().numpy().view(np.uint32), offs, kind)
     finally:
