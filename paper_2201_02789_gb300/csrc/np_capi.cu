@@ -135,7 +135,6 @@ np_status solve_multi(np_ctx* c, int kind, const np_csr* g, int nsrc, const int3
   NP_CK(cudaMemcpyAsync(c->ids, ids.data(), sizeof(int) * (size_t)nsrc, cudaMemcpyHostToDevice, s));
   const BodyKernels& K = kind == 0 ? bfs_kernels() : sssp64_kernels();
   np_config mcfg = serial_for(*cfg, nsrc, g->m);
-  mcfg.sweep_parents = 0;   // (the sweep covers single solves)
   Plan p = make_plan(K, mcfg);
   Args a;
   base_args(c->w, mcfg, a);
@@ -146,6 +145,8 @@ np_status solve_multi(np_ctx* c, int kind, const np_csr* g, int nsrc, const int3
   a.b.dist = dist;
   a.b.stamp = wsp<int>(c->w, c->w.lay.off_stamp);
   a.b.vmask = (int)(ld - 1);
+  // a swept frontier sweeps every query's state (padding entries stay unreached)
+  if (p.sweep) a.n_vertices = (int)total;
   if (kind == 1) {
     NP_TRY(ensure_dtag(c, total));
     a.b.dtag = c->dtag;
@@ -290,6 +291,7 @@ np_status np_config_default(np_config* cfg) {
   cfg->parent_grid = 0;
   cfg->serial = NP_SERIAL_SPREAD;
   cfg->small_parents = NP_SMALL_PARENTS_MAX;
+  cfg->sweep_parents = 4096;
   return NP_OK;
 }
 

@@ -512,9 +512,9 @@ BodyArgs child_body(const Args& a, bool level_mode) {
 // CTAs of the frontier sweep: kSweepVertices state elements each, at most as
 // many as the resident child grid (the sweep loops over the rest).
 int sweep_grid(const Args& a, const Grids& g) {
-  const int need = (a.n_vertices + kSweepVertices - 1) / kSweepVertices;
+  const int64_t need = ((int64_t)a.n_vertices + kSweepVertices - 1) / kSweepVertices;
   const int cap = g.cgrid > 0 ? g.cgrid : 1;
-  return need < 1 ? 1 : (need > cap ? cap : need);
+  return need < 1 ? 1 : (need > cap ? cap : (int)need);
 }
 
 // Enqueues the grids of one level (level mode, at body position k) or of one

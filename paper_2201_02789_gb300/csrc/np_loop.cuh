@@ -301,12 +301,13 @@ __global__ void __launch_bounds__(256) frontier_sweep_kernel(Args a) {
   const unsigned want = (unsigned)(L + 1);
   int* next = (L & 1) ? a.fr0 : a.fr1;
   int* next_count = &st->count[(L + 1) % 3];
-  for (int c0 = (int)blockIdx.x * kSweepVertices; c0 < n; c0 += (int)gridDim.x * kSweepVertices) {
+  // (64-bit range arithmetic: a multi-query state may come close to 2^31 elements)
+  for (long long c0 = (long long)blockIdx.x * kSweepVertices; c0 < n; c0 += (long long)gridDim.x * kSweepVertices) {
     bool mark[KV];
     unsigned mine = 0;
 #pragma unroll
     for (int k = 0; k < KV; k++) {
-      const int v = c0 + k * 256 + (int)threadIdx.x;
+      const long long v = c0 + k * 256 + (int)threadIdx.x;
       if (KIND == 0)
         mark[k] = v < n && (unsigned)__ldcg(&a.b.level[v]) == want;
       else
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(256) frontier_sweep_kernel(Args a) {
     int pos = s_base + (int)ex;
 #pragma unroll
     for (int k = 0; k < KV; k++)
-      if (mark[k]) next[pos++] = c0 + k * 256 + (int)threadIdx.x;
+      if (mark[k]) next[pos++] = (int)(c0 + k * 256 + (int)threadIdx.x);   // < n <= INT_MAX
     __syncthreads();   // s_base is rewritten by the next range's reservation
   }
 }

@@ -362,7 +362,9 @@ np_status np_server_create(np_ctx* ctx, const np_csr* graphs, int32_t ngraphs, c
       }
       p.S = S;
       p.cfg = serial_for(p.cfg, S, p.g.m);
-      p.cfg.sweep_parents = 0;   // (the frontier sweep covers single solves)
+      // (queries join a pool's frontier between steps by appending to it: the
+      // pools' frontiers append)
+      p.cfg.sweep_parents = 0;
       sv->pools.push_back(p);
       st = init_pool(sv, sv->pools.back());
     }

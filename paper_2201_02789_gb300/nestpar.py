@@ -25,6 +25,7 @@ NP_GRAN_NONE, NP_GRAN_WARP, NP_GRAN_BLOCK, NP_GRAN_MULTIBLOCK, NP_GRAN_GRID_DEVI
 NP_SCAN_LOOKBACK, NP_SCAN_ATOMIC = 0, 1
 NP_DRIVER_AUTO, NP_DRIVER_HOST, NP_DRIVER_CHUNK, NP_DRIVER_WHILE, NP_DRIVER_PERSISTENT = range(5)
 NP_SERIAL_SPREAD, NP_SERIAL_PACKED, NP_SERIAL_BLOCK = 0, 1, 2
+NP_SMALL_PARENTS_MAX = 2048
 NP_COUNT_CSR_DEGREE, NP_COUNT_BEZIER = 0, 1
 NP_BODY_BFS_VISIT, NP_BODY_SSSP_RELAX, NP_BODY_BEZIER_EVAL, NP_BODY_TRIANGLES = 0, 1, 2, 3
 NP_TRI_SLOTS = 256

@@ -43,7 +43,8 @@ def form_grid():
              ("mb3", npb.NP_GRAN_MULTIBLOCK, {"group_blocks": 3}),
              ("mb8", npb.NP_GRAN_MULTIBLOCK, {"group_blocks": 8}),
              ("griddev", npb.NP_GRAN_GRID_DEVICE, {}),
-             ("gridhost-spread", npb.NP_GRAN_GRID_HOST, {"serial": npb.NP_SERIAL_SPREAD}),
+             # (appending frontier: the library default sweeps levels of 4096 parents or more)
+             ("gridhost-spread", npb.NP_GRAN_GRID_HOST, {"serial": npb.NP_SERIAL_SPREAD, "sweep_parents": 0}),
              ("gridhost-block", npb.NP_GRAN_GRID_HOST, {"serial": npb.NP_SERIAL_BLOCK}),
              ("gridhost-packed", npb.NP_GRAN_GRID_HOST, {"serial": npb.NP_SERIAL_PACKED}),
              # (the small-level loop off, so that the grids and the sweep run every level)

@@ -91,6 +91,7 @@ def test_host_only_entry_points(lib):
     cfg = npb.np_config_default()
     assert (cfg.variant, cfg.threshold, cfg.cfactor, cfg.granularity, cfg.scan) == (1, 32, 4, npb.NP_GRAN_GRID_HOST, npb.NP_SCAN_ATOMIC)
     assert cfg.child_block == 64
+    assert (cfg.small_parents, cfg.sweep_parents) == (npb.NP_SMALL_PARENTS_MAX, 4096)
     assert npb.np_workspace_size(1 << 20, cfg) > (1 << 20) * 16
     with pytest.raises(npb.NestparError):
         npb.np_workspace_size(-1, cfg)

@@ -43,7 +43,10 @@ MULTI_FORMS = [("nodp", npb.config("nodp")), ("tca", npb.config("tca")),
                ("tca-T1-C1", npb.config("tca", threshold=1, cfactor=1)),
                ("cdp-chunk", npb.config("cdp")),
                ("block", npb.config("tca", granularity="block", threshold=4)),
-               ("mb3-lb", npb.config("tca", granularity="multiblock", group_blocks=3, scan=npb.NP_SCAN_LOOKBACK))]
+               ("mb3-lb", npb.config("tca", granularity="multiblock", group_blocks=3, scan=npb.NP_SCAN_LOOKBACK)),
+               # swept frontier over every query's state: every grid level, or levels of 100+ parents
+               ("sweep", npb.config("tca", sweep_parents=1, small_parents=0)),
+               ("sweep-mixed", npb.config("tca", sweep_parents=100))]
 
 
 @pytest.mark.parametrize("name,cfg", MULTI_FORMS, ids=[f[0] for f in MULTI_FORMS])
@@ -66,6 +69,32 @@ def test_multi_source_rows_equal_single_solves(ctx, name, cfg):
         np.testing.assert_array_equal(d_h[q, :g.n], oracle.sssp(g.row_ptr, g.col, g.w, int(s)))
         assert (lv_h[q, g.n:] == -1).all() and (d_h[q, g.n:] == 0xFFFFFFFF).all()
     assert st["parents"] == sum(int((oracle.bfs(g.row_ptr, g.col, int(s)) >= 0).sum()) for s in srcs)
+
+
+@pytest.mark.parametrize("sweep", [0, 1, 5000], ids=["append", "sweep", "sweep-large-levels"])
+def test_multi_source_larger_graph(ctx, sweep):
+    """16 queries on an R-MAT scale-16 graph (2^20 state elements: many sweep CTAs and
+    parent tiles per level), every row against the oracle."""
+    g = gen.rmat(16, 16, seed=23)
+    dg = DevGraph(g)
+    srcs = gen.random_sources(g, 16, seed=24)
+    ld = npb.multi_stride(g.n)
+    cfg = npb.config("tca", sweep_parents=sweep)
+    lv = torch.full((len(srcs), ld), 7, dtype=torch.int32, device=DEV)
+    dist = torch.full((len(srcs), ld), 7, dtype=torch.int32, device=DEV)
+    _, st = npb.np_bfs_multi(ctx.handle, dg.csr, srcs, lv, ld, cfg, stats=True)
+    assert st["error"] == 0
+    _, st = npb.np_sssp_multi(ctx.handle, dg.csr, srcs, dist, ld, cfg, stats=True)
+    assert st["error"] == 0
+    lv_h = lv.cpu().numpy()
+    d_h = dist.cpu().numpy().view(np.uint32)
+    with ThreadPoolExecutor(8) as ex:
+        refs = list(ex.map(lambda s: (oracle.bfs(g.row_ptr, g.col, int(s)), oracle.sssp(g.row_ptr, g.col, g.w, int(s))),
+                           srcs))
+    for q, (rl, rd) in enumerate(refs):
+        np.testing.assert_array_equal(lv_h[q, :g.n], rl)
+        np.testing.assert_array_equal(d_h[q, :g.n], rd)
+        assert (lv_h[q, g.n:] == -1).all() and (d_h[q, g.n:] == 0xFFFFFFFF).all()
 
 
 def test_multi_source_argument_errors(ctx):
@@ -142,7 +171,8 @@ def test_batch_tune_then_run(ctx):
             assert c["tuned_ms"] > 0 and c["candidates"] in (17, 18)
             cfg = c["config"]
             assert cfg["variant"] == npb.NP_VARIANT_NODP or cfg["granularity"] == npb.NP_GRAN_GRID_HOST
-            assert cfg["sweep_parents"] in (0, 1)
+            # (the candidates keep the class's own value, the library default here)
+            assert cfg["sweep_parents"] in (npb.np_config_default().sweep_parents, 1)
         out.fill_(3)
         _, st = npb.np_batch_run(b, out, stats=True)
         assert st["error"] == 0
