@@ -150,8 +150,11 @@ __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditional
     if (count <= 0 || count > limit || L >= max_levels) break;
     const int* ids = staged >= 0 ? s_stage : ((L & 1) ? a.fr1 : a.fr0);
     int pid[PPT], base[PPT], N[PPT];
+    unsigned aux[PPT];
     bool valid[PPT];
     unsigned mine = 0;
+    BodyArgs b = a.b;
+    b.L = L;
 #pragma unroll
     for (int r = 0; r < PPT; r++) {
       const int i = PPT * tid + r;
@@ -160,6 +163,8 @@ __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditional
       base[r] = 0;
       N[r] = 0;
       if (valid[r]) Body::count(a, pid[r], base[r], N[r]);
+      // (the value a staged parent carries, loaded beside its row bounds)
+      aux[r] = valid[r] ? Body::aux(b, pid[r]) : 0u;
       mine += (unsigned)N[r];
     }
     unsigned e0, e1, items, t1;
@@ -169,8 +174,6 @@ __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditional
       level_open(st, L, count);
       s_stage_n = 0;
     }
-    BodyArgs b = a.b;
-    b.L = L;
     b.next = (L & 1) ? a.fr0 : a.fr1;
     b.next_count = &st->count[(L + 1) % 3];
     {
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditional
           s_first[i] = (int)first;
           s_pid[i] = pid[r];
           s_base[i] = base[r];
-          s_aux[i] = valid[r] ? Body::aux(b, pid[r]) : 0u;
+          s_aux[i] = aux[r];
         }
         first += (unsigned)N[r];
       }
