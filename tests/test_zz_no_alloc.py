@@ -52,11 +52,13 @@ def _noalloc(c_d, nc, cap, cfg, spare=0):
 
 FORMS = [("tca", {}), ("tca", dict(scan=npb.NP_SCAN_ATOMIC, threshold=0, cfactor=2)),
          ("tca", dict(serial=npb.NP_SERIAL_BLOCK, parent_block=512)), ("nodp", {}),
-         ("nodp", dict(granularity="none"))]
+         ("nodp", dict(granularity="none")),
+         # every curve in its parent warp (the tessellation benchmark's form)
+         ("tca", dict(threshold=npb.INT32_MAX, parent_block=512))]
 
 
 @pytest.mark.parametrize("form,kw", FORMS, ids=["grid-host", "grid-host-atomic", "grid-host-cta-serial", "nodp",
-                                                "nodp-cta-tiles"])
+                                                "nodp-cta-tiles", "grid-host-no-child"])
 def test_noalloc_matches_oracle_and_np_bezier_two_calls(ctx, form, kw):
     cfg = npb.config(form, **kw)
     # first call: the largest input the static scratch allows; second call: a
