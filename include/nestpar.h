@@ -110,10 +110,11 @@ typedef int32_t np_status;
  *                     records in shared memory and searches there. */
 #define NP_SMALL_PARENTS_MAX 2048
 
-/* How a level loop forms the next frontier. By default children append each
- * vertex they reach (the relaxation's or claim's atomic returns the old value
- * to decide it; one atomic per warp batch reserves the places). With
- * sweep_parents > 0 (np_bfs / np_sssp, their _multi forms and the classes of a batch; grid-host
+/* How a level loop forms the next frontier. Children append each vertex they
+ * reach (the relaxation's or claim's atomic returns the old value to decide
+ * it; one atomic per warp batch reserves the places), except with
+ * sweep_parents > 0 (np_bfs / np_sssp, their _multi forms, the classes of a batch and the
+ * pools of a server, whose sweeps skip the slots holding no query; grid-host
  * aggregation with NP_SERIAL_SPREAD, graph / chunk / host driver), a level with
  * at least that many parents instead has its children only reduce (a fire-and-forget atomic
  * min of the level, or of the packed distance and tag), and a sweep over the
@@ -144,7 +145,7 @@ typedef struct np_config {
                             of each body one CTA runs whole levels itself while the frontier
                             has at most this many parents (<= NP_SMALL_PARENTS_MAX) and at
                             most 16384 children in all; 0 = off */
-  int32_t sweep_parents; /* np_bfs / np_sssp / batch classes: levels with at least this many parents form the
+  int32_t sweep_parents; /* level loops: levels with at least this many parents form the
                             next frontier by a sweep (see below); 0 = every level appends */
   int32_t reserved[1];   /* must be zero */
 } np_config;

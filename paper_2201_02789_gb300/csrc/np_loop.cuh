@@ -304,8 +304,11 @@ __global__ void __launch_bounds__(256) frontier_sweep_kernel(Args a) {
   const unsigned want = (unsigned)(L + 1);
   int* next = (L & 1) ? a.fr0 : a.fr1;
   int* next_count = &st->count[(L + 1) % 3];
+  const int* busy = a.sweep_busy;
   // (64-bit range arithmetic: a multi-query state may come close to 2^31 elements)
   for (long long c0 = (long long)blockIdx.x * kSweepVertices; c0 < n; c0 += (long long)gridDim.x * kSweepVertices) {
+    // a chunk lies in one slot; an idle slot's state holds no vertex of this level (uniform over the CTA)
+    if (busy && !busy[c0 >> a.sweep_lg]) continue;
     bool mark[KV];
     unsigned mine = 0;
 #pragma unroll

@@ -201,6 +201,15 @@ np_status build_pool_graph(np_server* sv, Pool& p) {
   a.b.stamp = wsp<int>(p.ws, p.ws.lay.off_stamp);
   a.b.vmask = (1 << p.lg) - 1;
   const int64_t elems = (int64_t)p.S << p.lg;
+  if (plan.sweep) {
+    // the sweep covers every slot's state; with slots of at least one sweep
+    // chunk it skips the slots this step's admission table marks idle
+    a.n_vertices = (int)elems;
+    if ((1 << p.lg) >= kSweepVertices) {
+      a.sweep_lg = p.lg;
+      a.sweep_busy = reinterpret_cast<const int*>(ctl_adm(p.d_ctl) + p.S);
+    }
+  }
   Grids gr = grids_for(e, plan, p.cfg, elems);
   cudaStream_t cs = e.cap_stream;
   NP_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -362,9 +371,8 @@ np_status np_server_create(np_ctx* ctx, const np_csr* graphs, int32_t ngraphs, c
       }
       p.S = S;
       p.cfg = serial_for(p.cfg, S, p.g.m);
-      // (queries join a pool's frontier between steps by appending to it: the
-      // pools' frontiers append)
-      p.cfg.sweep_parents = 0;
+      // (a pool's swept frontier sweeps its busy slots only: see build_pool_graph)
+      if (((int64_t)S << p.lg) > (int64_t)INT_MAX) p.cfg.sweep_parents = 0;
       sv->pools.push_back(p);
       st = init_pool(sv, sv->pools.back());
     }

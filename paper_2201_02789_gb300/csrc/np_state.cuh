@@ -230,7 +230,10 @@ struct Args {
   int small_parents;             // > 0: the while body's one-CTA loop runs levels of at most this many parents
   int n_vertices;                // swept frontier: state elements the sweep visits
   int sweep_parents;             // swept frontier: levels with at least this many parents sweep (0 = none)
-  int pad3;
+  // swept frontier of a serving pool: the sweep skips the chunks of slots
+  // that hold no query (slot = element >> sweep_lg, sweep_lg >= 11), or NULL
+  int sweep_lg;
+  const int* sweep_busy;
 };
 
 struct AggSeg {

@@ -250,10 +250,13 @@ def serve_graphs():
     return graphs, [DevGraph(g) for g in graphs]
 
 
-def test_server_alone_equals_mix(ctx, serve_graphs):
+# (swept frontier: the default's levels of 4096+ parents, or every level; the scale-9 pool's slots
+# are smaller than a sweep chunk, so it sweeps every slot, the others skip the idle ones)
+@pytest.mark.parametrize("sweep", [{}, dict(sweep_parents=1)], ids=["default", "sweep-every-level"])
+def test_server_alone_equals_mix(ctx, serve_graphs, sweep):
     graphs, devs = serve_graphs
     sv = npb.np_server_create(ctx.handle, [d.csr for d in devs], max_slots=3, levels_per_step=2,
-                              bfs_cfg=npb.config("tca"), sssp_cfg=npb.config("tca", threshold=8))
+                              bfs_cfg=npb.config("tca", **sweep), sssp_cfg=npb.config("tca", threshold=8, **sweep))
     try:
         rng = np.random.default_rng(0)   # order of arrivals only; sources come from gen
         queries = []
