@@ -26,6 +26,10 @@ arrivals of BFS/SSSP queries from random sources over seven resident R-MAT
 graphs of scales 16..22; queries/s at saturation and p50/p99 latency at
 0.5/0.8/0.95 of it).
 
+On one GPU the default run then measures every other workload, each in a
+process of its own with few steps and a one-solve CPU leg (the oracle check),
+and adds their figures to its JSON line as `other_workloads` (--no-others: not).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
 """
 from __future__ import annotations
@@ -613,6 +617,58 @@ def comparison_forms(npb, workload: str, cdp_steps: int):
             ("t_c_a_block", npb.config("tca", granularity="block"), 5)] + bt_only + graph_only
 
 
+# The other workloads, measured after the default (headline) run and summarised in its JSON line:
+# each runs in a process of its own with few steps and a one-solve CPU leg (which still checks the
+# result against the oracle). (name, extra arguments)
+OTHER_WORKLOADS = [("bfs-rmat20", ["--steps", "50"]), ("bt64k", ["--steps", "100"]), ("bt256k", ["--steps", "50"]),
+                   ("bfs4k", ["--steps", "100"]), ("tc-rmat17", ["--steps", "20"]),
+                   ("road", ["--steps", "5", "--cdp-steps", "1"]), ("batched-sssp", ["--steps", "5"]),
+                   ("batched-bfs", ["--steps", "5"]), ("serving", ["--steps", "5"])]
+OTHERS_SECONDS = 420   # no further workload starts after this much time
+
+
+def compact(d: dict) -> dict:
+    """The figures of a workload's JSON line that the headline line carries."""
+    out = {k: d[k] for k in ("metric", "value", "unit", "ms_per_step", "gpu_launches") if k in d}
+    r = d.get("roofline") or {}
+    if r:
+        out["roofline"] = {k: r.get(k) for k in ("kernel", "achieved", "peak", "frac", "traffic")}
+    if d.get("step_roofline"):
+        out["step_roofline_frac"] = d["step_roofline"].get("frac")
+    if d.get("e2e"):
+        out["e2e"] = {k: d["e2e"].get(k) for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
+    for k in ("parity_vs_oracle", "parity_vs_oracle_sample", "speedup_vs_plain_cdp", "speedup_vs_nodp",
+              "speedup_vs_sequential", "saturation", "poisson"):
+        if k in d:
+            out[k] = d[k]
+    out["clocks"] = d.get("clocks")
+    return out
+
+
+def run_other_workloads() -> dict:
+    """Runs OTHER_WORKLOADS one after another (one GPU); per workload its compact figures, the
+    command, or the error that stopped it."""
+    import subprocess
+    res = {}
+    t0 = time.perf_counter()
+    for name, extra in OTHER_WORKLOADS:
+        if time.perf_counter() - t0 > OTHERS_SECONDS:
+            res[name] = {"skipped": "time cap of the default run reached"}
+            continue
+        cmd = ["python", "bench.py", "--workload", name, "--warmup", "3", "--cpu-seconds", "0.1",
+               "--e2e-steps", "2", "--no-others"] + extra
+        try:
+            r = subprocess.run([sys.executable] + cmd[1:], cwd=ROOT, capture_output=True, text=True, timeout=240)
+            lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+            if r.returncode != 0 or not lines:
+                res[name] = {"command": " ".join(cmd), "error": f"exit {r.returncode}: {r.stderr[-300:]}"}
+                continue
+            res[name] = dict(compact(json.loads(lines[-1])), command=" ".join(cmd))
+        except Exception as e:   # a failed side measurement never costs the headline line
+            res[name] = {"command": " ".join(cmd), "error": repr(e)[:300]}
+    return res
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_2201_02789_gb300 import build as nbuild
@@ -810,6 +866,10 @@ def run_ours(args, ws, rank, local):
             "forms": forms, "roofline": roofline, "step_roofline": step_roofline,
             "cpu_baseline": cpu, "parity_vs_oracle": parity, "e2e": e2e, "clocks": clocks,
             "gpu_launches": gpu_launches, "profile_breakdown": breakdown}
+    if ws == 1 and args.workload == "sssp-rmat20" and not args.no_others:
+        # the other workloads, each in a process of its own after this one's GPU work
+        torch.cuda.synchronize(dev)
+        line["other_workloads"] = run_other_workloads()
     print(json.dumps(line), flush=True)
     ctx.close()
     if distributed:
@@ -1301,6 +1361,8 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="time every variant of the paper's comparison on the workload (one JSON line each)")
     ap.add_argument("--variants", default="", help="with --sweep: comma-separated variant names to run")
+    ap.add_argument("--no-others", action="store_true",
+                    help="default run: do not measure the other workloads after the headline")
     ap.add_argument("--only-headline", action="store_true",
                     help="headline form and three profile-mode solves only (for profiler captures)")
     args = ap.parse_args()
