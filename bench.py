@@ -97,7 +97,8 @@ TUNED = {# tessellation: a threshold above every count, so that each curve's poi
          # 42 us with the aggregated child grid below (BT_CHILD_GRID); 512-thread parent CTAs make the
          # output-offset look-back groups 16 tiles long
          "bt64k": dict(threshold=2**31 - 1, parent_block=512),
-         "bt256k": dict(threshold=2**31 - 1, parent_block=512),
+         # (BT-256K: 448-thread parent CTAs, 66.7 against 68.7 us at 512; BT-64K the same at both)
+         "bt256k": dict(threshold=2**31 - 1, parent_block=448),
          "tc-rmat17": dict(threshold=8, child_block=32, cfactor=1),
          # SSSP: every grid level's children only reduce and a sweep over the vertex state forms the
          # next frontier (A/B on GB300: 454 -> 436 us; BFS, whose claims rarely reach the atomic,
