@@ -106,7 +106,11 @@ TUNED = {# tessellation: a threshold above every count, so that each curve's poi
          "sssp-rmat20": dict(sweep_parents=1),
          # BFS: the appending frontier (the library default sweeps levels of 4096 parents or more,
          # 184.6 against 178.5 us here)
-         "bfs-rmat20": dict(sweep_parents=0)}
+         "bfs-rmat20": dict(sweep_parents=0),
+         # road grid (out-degree <= 8): a threshold above every degree launches nothing, so no child
+         # grid runs at any level, and appending frontiers (a sweep reads the whole state for a
+         # frontier of about a tenth of it): 10.1 against 13.2 ms with the defaults
+         "road": dict(threshold=2**31 - 1, sweep_parents=0)}
 # the tessellation's best form with an aggregated child grid: T 32 (the default), 32-thread child
 # blocks of 4 original blocks, 512-thread parent CTAs spreading the serialised points over the CTA
 # (serial 2: NP_SERIAL_BLOCK); timed beside the headline
@@ -736,7 +740,9 @@ def run_ours(args, ws, rank, local):
         # init + while-body iterations x (unroll x (parent, child) + condition) (+ the SSSP
         # distances written from the packed state)
         # (the swept frontier adds its sweep kernel to every grid level)
-        per_level = 3 if cfg.sweep_parents > 0 else 2
+        # (a threshold that launches nothing runs no child grid, and a level that sweeps adds the sweep)
+        child_runs = not (cfg.threshold == npb.INT32_MAX and cfg.serial != npb.NP_SERIAL_PACKED)
+        per_level = 1 + (1 if child_runs else 0) + (1 if cfg.sweep_parents > 0 else 0)
         loop = 1 if cfg.driver == npb.NP_DRIVER_PERSISTENT else st["graph_iterations"] * (per_level * cfg.unroll + 1)
         pre = 1 if cfg.driver != npb.NP_DRIVER_PERSISTENT and cfg.small_parents > 0 else 0
         per_solve = 1 + pre + loop + (1 if wl["kind"] == "sssp" else 0)
@@ -853,8 +859,10 @@ def run_ours(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"bezier": "f32", "tc": "i32"}.get(wl["kind"], "u32"), "data": "synthetic",
             "config": dict(wl["config"], l2=L2_NOTE),
-            "form": ("threshold INT32_MAX (no child launches: the serialised children run in the parent "
-                     "warps, a whole warp per parent of 32 or more), " if cfg.threshold == npb.INT32_MAX else
+            "form": (("threshold INT32_MAX (no child launches: the serialised children run in the parent "
+                      "warps, a whole warp per parent of 32 or more), " if wl["kind"] == "bezier" else
+                      "threshold INT32_MAX (no child launches: the serialised children spread over the "
+                      "parent warps), ") if cfg.threshold == npb.INT32_MAX else
                      f"threshold {cfg.threshold} + coarsening {cfg.cfactor} ({cfg.child_block}-thread child blocks) "
                      "+ grid aggregation (atomic scan), ") + (
                         "one fixed pass replayed as a CUDA graph" if wl["kind"] in ("bezier", "tc") else

@@ -525,7 +525,7 @@ np_status enqueue_pass(const Plan& p, Args a, const Grids& g, bool level_mode, i
   const bool pdl = kPdl && p.mode != M_DEVICE_LAUNCH;
   void* pargs[] = {&a};
   NP_CK(launch_pdl(p.parent, dim3(g.pgrid), dim3(g.pblock), pargs, s, pdl));
-  if (p.mode == M_GRID_HOST && !(p.child_idle && !level_mode)) {
+  if (p.mode == M_GRID_HOST && !p.child_idle) {
     AggSeg seg = make_seg(a, g, level_mode);
     BodyArgs b = child_body(a, level_mode);
     void* cargs[] = {&b, &seg};
@@ -552,7 +552,7 @@ np_status profiled_pass(Engine& e, const Workspace& w, const Plan& p, Args a, co
   NP_CK(cudaLaunchKernel(p.parent, dim3(g.pgrid), dim3(g.pblock), pargs, 0, s));
   NP_CK(cudaEventRecord(e.ev[1], s));
   bool child = false, other = false;
-  if (p.mode == M_GRID_HOST && !(p.child_idle && !level_mode)) {
+  if (p.mode == M_GRID_HOST && !p.child_idle) {
     AggSeg seg = make_seg(a, g, level_mode);
     BodyArgs b = child_body(a, level_mode);
     void* cargs[] = {&b, &seg};

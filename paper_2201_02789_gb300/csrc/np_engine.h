@@ -54,7 +54,8 @@ struct Plan {
   const void* small = nullptr;  // one-CTA small-level loop before the while loop and at each body's end (grid-host)
   const void* sweep = nullptr;  // swept frontier: the kernel that rebuilds the next frontier after each level
   // grid-host form that can give its child grid no work (threshold INT32_MAX,
-  // serialised children in the parent kernel): a fixed pass launches no child
+  // serialised children in the parent kernel): no child grid is launched (a
+  // fixed pass, or each level of a level loop)
   bool child_idle = false;
   int mode = M_NODP;
   int gran = G_NODP;
