@@ -112,3 +112,22 @@ def test_poisson_arrivals_are_seeded_and_have_the_offered_rate():
     # exponential gaps: mean 1/rate, coefficient of variation 1 (20,000 samples: within 3%)
     assert abs(gaps.mean() * 500.0 - 1.0) < 0.03
     assert abs(gaps.std() / gaps.mean() - 1.0) < 0.03
+
+
+def test_other_workloads_of_the_default_run():
+    """Every workload the default run adds is a bench workload other than the headline, run with
+    a one-solve CPU leg (which keeps the oracle check) and without recursing into further runs;
+    compact() keeps the figures a reader checks and drops the rest."""
+    names = [n for n, _ in bench.OTHER_WORKLOADS]
+    assert len(set(names)) == len(names) and "sssp-rmat20" not in names
+    assert set(names) == set(bench.WORKLOADS) - {"sssp-rmat20"}
+    line = {"metric": "m", "value": 2.0, "unit": "GTEPS", "ms_per_step": 1.5, "gpu_launches": 10,
+            "roofline": {"kernel": "child_agg", "achieved": 1.0, "peak": 2.0, "frac": 0.5, "traffic": None,
+                         "avg_launch_ms": 0.1},
+            "step_roofline": {"frac": 0.25, "algorithmic_bytes": 3},
+            "e2e": {"value": 1.0, "unit": "GTEPS", "h2d_bytes_per_step": 4, "d2h_bytes_per_step": 5, "mode": "x"},
+            "parity_vs_oracle": True, "forms": {"nodp": {}}, "clocks": {"sm_mhz": 2070.0}}
+    c = bench.compact(line)
+    assert c["value"] == 2.0 and c["roofline"]["frac"] == 0.5 and "avg_launch_ms" not in c["roofline"]
+    assert c["step_roofline_frac"] == 0.25 and c["e2e"]["h2d_bytes_per_step"] == 4 and "mode" not in c["e2e"]
+    assert c["parity_vs_oracle"] is True and "forms" not in c and c["clocks"]["sm_mhz"] == 2070.0
