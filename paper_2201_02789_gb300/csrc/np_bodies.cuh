@@ -54,7 +54,7 @@ struct BfsBody {
     for (int k = 0; k < K; k++) {
       v[k] = f[k].v;
       cur[k] = 0;
-      if (valid[k]) cur[k] = NP_FILTER_LOAD(&b.level[v[k]]);
+      if (valid[k]) cur[k] = b.unfiltered ? -1 : NP_FILTER_LOAD(&b.level[v[k]]);
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -296,7 +296,7 @@ struct Sssp64Body {
       live[k] = p[k].du != 0xffffffffu;
       const unsigned long long s = (unsigned long long)p[k].du + f[k].w;
       nd[k] = ((s >= 0xffffffffull ? 0xfffffffeull : s) << 32) | tag;
-      cur[k] = (valid[k] && live[k]) ? NP_FILTER_LOAD(&b.dtag[v[k]]) : 0ull;
+      cur[k] = (valid[k] && live[k]) ? (b.unfiltered ? ~0ull : NP_FILTER_LOAD(&b.dtag[v[k]])) : 0ull;
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {

@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(1024) level_small(Args a, cudaGraphConditional
     unsigned mine = 0;
     BodyArgs b = a.b;
     b.L = L;
+    b.unfiltered = 1;
 #pragma unroll
     for (int r = 0; r < PPT; r++) {
       const int i = PPT * tid + r;

@@ -187,7 +187,10 @@ struct BodyArgs {
   unsigned long long* acc;       // triangle counting: kTcSlots partial counts
   unsigned long long* dtag;      // SSSP, packed form: dist << 32 | tag per vertex
   int sweep;                     // 1: this level's children reduce, the frontier sweep appends
-  int pad;
+  // 1: no filter read before a visit's or relaxation's atomic (the one-CTA
+  // small-level loop: its atomics are few, and the read would only lengthen
+  // each item's chain of round trips)
+  int unfiltered;
 };
 
 struct Args {
